@@ -1,0 +1,196 @@
+"""Seeded synthetic workloads for the ETD membrane step.
+
+This module builds initial fields and parameter sets only: grid coordinates, the tanh
+membrane profiles of the paper's experiments (Sec. 4.1, Sec. 4.3), seeded random protein
+fields and the model coefficients.  It holds none of the time-stepping arithmetic, so both
+the CUDA path and the CPU oracle can take their inputs from here without sharing any of the
+method's code.
+
+Conventions (shared by both sides):
+  * A field on an (Nz, Ny, Nx) grid is a C-ordered array with x fastest; 2D grids use
+    shape (Ny, Nx).
+  * Grid points are x_i = -X + i*h, i = 0..N-1, h = 2X/N, on the periodic box
+    [-X, X)^d (Sec. 2.1).
+  * Phase field Phi in (0, 1) with wells at 0 and 1, protein density U in [0, 1] (Sec. 1).
+    A configuration written in the (-1, 1) convention, phi = tanh((R - r)/(sqrt(2) eps)),
+    maps to Phi = (1 + phi)/2, which is the paper's profile 0.5 + 0.5 tanh(3 (r0 - r)/eps_phi)
+    with eps_phi = 3 sqrt(2) eps.  The protein width is eps_u = eps_phi / 2 (Sec. 4.3 uses
+    eps_phi = 10h, eps_u = 5h).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class ModelParams:
+    """Model and scheme coefficients, named as in Eq. (1.1)-(1.2), (3.1)-(3.2)."""
+    dim: int = 3
+    n: tuple = (64, 64, 64)          # (Nx, Ny, Nz); Nz = 1 for dim = 2
+    half_len: tuple = (math.pi, math.pi, math.pi)   # (X, Y, Z), box [-X, X)
+    scheme: int = 2                  # 1 = ETD1, 2 = ETDRK2
+    model: int = 1                   # 0 = fixed membrane (Sec. 2), 1 = coupled (Sec. 3)
+    precision: int = 0               # 0 = FP64, 1 = FP32 storage/FFT with FP64 tables/reductions
+    tau: float = 1e-4
+    eps_phi: float = 0.1
+    eps_u: float = 0.05
+    mu: float = 2.0
+    lambda_surf: float = 10.0
+    kappa: float = 1.0
+    lambda_line: float = 30.0
+    M_area: float = 100.0
+    A0: float = float("nan")         # NaN: taken as <Phi^0, 1>_h on the first step
+    alpha: float = 700.0
+    u0: float = 0.0
+    gamma: float = 15000.0
+    M: float = 3000.0
+    ubar: float = 0.3
+    A1: float = 20.0
+    A2: float = 50.0
+    B1: float = 1.0
+    B2: float = 1000.0
+    band_mask_hi: float = 0.99       # band = {|2 Phi - 1| < 0.99}
+    recover_delta: float = 1e-3      # U = GU/G where G > 1e-3 (Sec. 3.3)
+    cg_rtol: float = 1e-13
+    cg_maxit: int = 20000
+    linear_only: int = 0             # test mode: nonlinear terms R1 = R2 = 0
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.n
+        return (ny, nx) if self.dim == 2 else (nz, ny, nx)
+
+    @property
+    def h(self):
+        return tuple(2.0 * X / N for X, N in zip(self.half_len, self.n))
+
+    def replace(self, **kw) -> "ModelParams":
+        return dataclasses.replace(self, **kw)
+
+
+def eps_from_cfg(eps_cfg: float):
+    """Map a (-1,1)-convention width to (eps_phi, eps_u) of the paper's convention."""
+    eps_phi = 3.0 * math.sqrt(2.0) * eps_cfg
+    return eps_phi, 0.5 * eps_phi
+
+
+def grid(n, half_len, dim):
+    """Coordinate arrays of the periodic grid, broadcastable to the field shape."""
+    nx, ny, nz = n
+    X, Y, Z = half_len
+    x = -X + np.arange(nx) * (2.0 * X / nx)
+    y = -Y + np.arange(ny) * (2.0 * Y / ny)
+    if dim == 2:
+        return x[None, :], y[:, None]
+    z = -Z + np.arange(nz) * (2.0 * Z / nz)
+    return x[None, None, :], y[None, :, None], z[:, None, None]
+
+
+def tanh_profile(dist_inside, eps_cfg):
+    """Phi = 0.5 + 0.5 tanh(d / (sqrt(2) eps)); d > 0 inside the membrane."""
+    return 0.5 + 0.5 * np.tanh(dist_inside / (math.sqrt(2.0) * eps_cfg))
+
+
+def sphere_phi(p: ModelParams, radius, eps_cfg, center=(0.0, 0.0, 0.0)):
+    c = grid(p.n, p.half_len, p.dim)
+    r2 = sum((ci - c0) ** 2 for ci, c0 in zip(c, center))
+    return tanh_profile(radius - np.sqrt(r2), eps_cfg) * np.ones(p.shape)
+
+
+def ellipsoid_phi(p: ModelParams, semi_axes, eps_cfg):
+    """Scaled-radius ellipsoid, r = sqrt(x^2 + (a/b)^2 y^2 + (a/c)^2 z^2), r0 = a.
+
+    Same construction as the paper's 2D ellipse r = sqrt(x^2 + sqrt(3) y^2) (Sec. 4.2).
+    """
+    a, b, c_ = semi_axes
+    x, y, z = grid(p.n, p.half_len, 3)
+    r = np.sqrt(x ** 2 + (a / b) ** 2 * y ** 2 + (a / c_) ** 2 * z ** 2)
+    return tanh_profile(a - r, eps_cfg) * np.ones(p.shape)
+
+
+def two_spheres_phi(p: ModelParams, radii, centers, eps_cfg):
+    out = np.zeros(p.shape)
+    for R, c0 in zip(radii, centers):
+        out = np.maximum(out, sphere_phi(p, R, eps_cfg, c0))
+    return out
+
+
+def band_of(phi, hi=0.99):
+    """Indicator of the narrow band {|2 Phi - 1| < hi} used to place the initial protein."""
+    return np.abs(2.0 * phi - 1.0) < hi
+
+
+# ---------------------------------------------------------------------------------------
+# Named workloads.  Sizes and seeds follow the five configurations of the benchmark plan:
+#   c1  2D fixed membrane, ETD1, FP64, 128^2, circle R = 0.6 pi, eps = 0.05, seed 0
+#   c2  3D fixed membrane, ETDRK2, 128^3, sphere R = 0.5 pi, eps = 0.05, seed 1
+#   c3  3D coupled, ETDRK2, 256^3, ellipsoid (1.2, 0.9, 0.9), eps = 0.18, seed 2
+#   c4  batched fixed-membrane sweep (64^3/96^3/128^3), seeds 100-147
+#   c5  3D coupled, 512^3, two spheres R = 0.8, 0.6 at (+-0.8, 0, 0), seed 3
+# Every configuration lives on [-pi, pi)^d.  `n` overrides the grid (same physical setup
+# on a coarser grid, e.g. c3 at 64^3 for the oracle).
+# ---------------------------------------------------------------------------------------
+
+def _fixed_params(dim, n, eps_cfg, scheme, M, tau, precision):
+    eps_phi, eps_u = eps_from_cfg(eps_cfg)
+    return ModelParams(dim=dim, n=n, half_len=(math.pi,) * 3, scheme=scheme, model=0,
+                       precision=precision, tau=tau, eps_phi=eps_phi, eps_u=eps_u,
+                       gamma=100.0, M=M, ubar=0.5, B1=1.0, B2=2000.0)
+
+
+def _coupled_params(n, eps_cfg, tau, scheme, precision):
+    # Coefficients of the paper's 3D run (Sec. 4.3) except the membrane friction mu, raised
+    # from 2 to 200: on this machine and interface width the explicit advection of g u by
+    # v = -d_t phi grad phi/|grad phi|^2 is unstable at tau = 1e-4 with mu = 2 (|v| ~ 1e2
+    # to 1e5 at the band edge), and stays bounded with mu = 200 (|v| ~ 8).
+    eps_phi, eps_u = eps_from_cfg(eps_cfg)
+    return ModelParams(dim=3, n=n, half_len=(math.pi,) * 3, scheme=scheme, model=1,
+                       precision=precision, tau=tau, eps_phi=eps_phi, eps_u=eps_u,
+                       mu=200.0, lambda_surf=10.0, kappa=1.0, lambda_line=30.0,
+                       M_area=100.0, A1=20.0, A2=50.0, M=3000.0, B1=1.0, B2=1000.0,
+                       gamma=15000.0, alpha=700.0, ubar=0.3, u0=0.0)
+
+
+def workload(name: str, n: Optional[int] = None, precision: int = 0, scheme=None,
+             tau=None):
+    """Return (params, Phi0, U0, nsteps) for a named workload (float64 arrays)."""
+    if name == "c1":
+        N = n or 128
+        p = _fixed_params(2, (N, N, 1), 0.05, scheme or 1, 600.0, tau or 1e-3, precision)
+        phi = sphere_phi(p, 0.6 * math.pi, 0.05)
+        rng = np.random.default_rng(0)
+        u = 0.5 * (1.0 + rng.uniform(-0.1, 0.1, size=p.shape))
+        return p, phi, u, 100
+    if name == "c2":
+        N = n or 128
+        p = _fixed_params(3, (N, N, N), 0.05, scheme or 2, 200.0, tau or 1e-2, precision)
+        phi = sphere_phi(p, 0.5 * math.pi, 0.05)
+        rng = np.random.default_rng(1)
+        u = 0.5 * (1.0 + np.clip(0.1 * rng.standard_normal(size=p.shape), -1.0, 1.0))
+        return p, phi, u, int(round(0.04 / p.tau))
+    if name == "c3":
+        N = n or 256
+        p = _coupled_params((N, N, N), 0.18, tau or 1e-4, scheme or 2, precision)
+        phi = ellipsoid_phi(p, (1.2, 0.9, 0.9), 0.18)
+        rng = np.random.default_rng(2)
+        xi = rng.uniform(-0.05, 0.05, size=p.shape)
+        u = np.where(band_of(phi), 0.5 * (1.0 + xi), 0.5)
+        return p, phi, u, 500
+    if name == "c5":
+        N = n or 512
+        p = _coupled_params((N, N, N), 0.18, tau or 5e-5, scheme or 2, precision)
+        phi = two_spheres_phi(p, (0.8, 0.6), ((-0.8, 0, 0), (0.8, 0, 0)), 0.18)
+        rng = np.random.default_rng(3)
+        xi = rng.uniform(-0.05, 0.05, size=p.shape)
+        u = np.where(band_of(phi), 0.5 * (1.0 + xi), 0.5)
+        return p, phi, u, 2000
+    raise KeyError(name)
+
+
+def random_fields(shape, seed, lo=0.0, hi=1.0):
+    """Plain seeded uniform field (used by unit tests of single operators)."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=shape)
