@@ -1,0 +1,168 @@
+/*
+ * etd.h -- C ABI of the GB300 ETD step for the phase-field model of multicomponent
+ * membranes (Luo, Qiao, Zhao: exponential time differencing schemes for a phase-field
+ * model of multicomponent membranes).
+ *
+ * The library advances the phase field phi (membrane) and the protein density u on a
+ * periodic 2D/3D grid with the FFT-based stabilised ETD1/ETDRK2 schemes of Sec. 3.3 and
+ * Algorithm 1, or (model = ETD_MODEL_FIXED) the protein density alone on a frozen membrane.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are dense, C-ordered, x fastest: index (k*Ny + j)*Nx + i for 3D, j*Nx + i for
+ *    2D.  Grid point (i,j,k) sits at (-X + i*hx, -Y + j*hy, -Z + k*hz), h = 2X/N (Sec. 2.1).
+ *  - Element type is double for ETD_FP64 and float for ETD_FP32_MIXED.  FP32_MIXED keeps
+ *    the phi-function tables (built in FP64, rounded once), every reduction (mass, volume,
+ *    energy, CG dot products) and the scalar constraint terms in FP64.
+ *  - Field pointers are DEVICE pointers owned by the caller (for example PyTorch tensors
+ *    on the plan's device).  They must stay valid until the enqueued work completes.  The
+ *    library never frees them.  All work is enqueued on the stream given to etd_plan.
+ *  - The plan owns its workspace (spectra, band list, CG vectors, tables) and frees it
+ *    in etd_free.  A plan is not thread-safe; use one plan per host thread.
+ *  - No C++ exception crosses this boundary.  Errors come back as etd_status; the
+ *    message of the last error of the calling thread is returned by etd_last_error().
+ *  - Supported grids: every N a power of two, 8 <= N <= 256 along x and y, N_z in
+ *    {1 (2D)} or 8..256, cubic boxes X = Y (= Z).  Other sizes return ETD_EINVAL.
+ */
+#ifndef ETD_H
+#define ETD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct etd_plan_s *etd_plan_t;
+
+typedef enum {
+  ETD_OK = 0,
+  ETD_EINVAL = 1,      /* invalid argument or unsupported size                        */
+  ETD_ENOMEM = 2,      /* device allocation failed                                    */
+  ETD_ECUDA = 3,       /* a CUDA runtime call failed                                  */
+  ETD_ENONFINITE = 4,  /* a non-finite value appeared in the state                    */
+  ETD_ENOTCONV = 5,    /* band CG did not reach cg_rtol within cg_maxit iterations     */
+  ETD_ETIMEOUT = 6,    /* a grid-wide barrier of a persistent kernel gave up waiting   */
+  ETD_EMBP = 7         /* reserved: maximum bound violated beyond tolerance           */
+} etd_status;
+
+typedef enum { ETD_ETD1 = 1, ETD_ETDRK2 = 2 } etd_scheme;
+typedef enum { ETD_MODEL_FIXED = 0, ETD_MODEL_COUPLED = 1 } etd_model;
+typedef enum { ETD_FP64 = 0, ETD_FP32_MIXED = 1 } etd_precision;
+
+/* Problem statement (Sec. 1 model, Sec. 3.1 splittings, Sec. 3.3 schemes). */
+typedef struct {
+  int dim;                 /* 2 or 3                                                  */
+  int n[3];                /* (Nx, Ny, Nz); Nz = 1 when dim = 2                        */
+  double half_len[3];      /* (X, Y, Z): box [-X,X) x [-Y,Y) x [-Z,Z)                   */
+  int scheme;              /* etd_scheme                                              */
+  int model;               /* etd_model                                               */
+  int precision;           /* etd_precision                                           */
+  double tau;              /* time step (Sec. 2.2, Sec. 3.3)                          */
+  double eps_phi, eps_u;   /* interface widths of phi and u (Eq. (1.1)-(1.2))          */
+  double mu, lambda_surf, kappa, lambda_line, M_area, A0, alpha, u0;  /* Eq. (1.1)     */
+  double gamma, M, ubar;   /* nonlocal strength, mass penalty, mean density (Eq. (1.2)) */
+  double A1, A2, B1, B2;   /* stabilisers of Eq. (3.1) and Eq. (3.2)                  */
+  double band_mask_hi;     /* narrow band = {|2 phi - 1| < band_mask_hi}, e.g. 0.99    */
+  double recover_delta;    /* U = GU/G where G > recover_delta (Sec. 3.3), e.g. 1e-3    */
+  double cg_rtol;          /* relative residual of the band CG                         */
+  int cg_maxit;            /* iteration cap of the band CG                             */
+  int linear_only;         /* 1: drop R1 and R2 (the exact linear flow; tests)          */
+} etd_params;
+
+/* Diagnostics of the current state (Eq. (2.16) energy and the bound of Sec. 2.2). */
+typedef struct {
+  double energy;           /* E_{phi,h}[U] of Eq. (2.16), band-restricted inverse      */
+  double mass;             /* fixed: <g (f(U)-ubar),1>_h ; coupled: <g (U-ubar),1>_h    */
+  double max_bound;        /* max |2U-1| over {G > recover_delta}                       */
+  double umin, umax;       /* min/max U over {G > recover_delta}                        */
+  double volume;           /* <phi,1>_h                                                */
+  long band_size;          /* number of band nodes                                     */
+  int cg_iters_last;       /* iterations of the last band solve                        */
+  double cg_resid_last;    /* relative residual reached by the last band solve         */
+} etd_diag;
+
+/* Create a plan: validates `params`, allocates the workspace on the current device and
+ * builds the phi-function tables in FP64 (phi_0, tau phi_1, tau phi_2 of tau l^phi and
+ * tau l^u, Sec. 3.2-3.3).  `cuda_stream` is a cudaStream_t (NULL = legacy stream).
+ * Returns ETD_EINVAL for unsupported sizes or non-positive tau/eps, ETD_ENOMEM when the
+ * workspace does not fit.  On failure *out is NULL. */
+etd_status etd_plan(const etd_params *params, void *cuda_stream, etd_plan_t *out);
+
+/* Advance `nsteps` steps in place (Algorithm 1; ETD1 or ETDRK2 per params.scheme).
+ * coupled: phi and u are both read and overwritten.
+ * fixed:   phi is read when non-NULL (it then fixes G = g(phi) and the band for this and
+ *          later calls) and is never written; the first call must pass it.
+ * When A0 was NaN at plan time, the first call fixes A0 = <phi,1>_h.
+ * Asynchronous unless `last` is non-NULL: then the call synchronises the stream, checks
+ * the state for non-finite values and the CG status, and fills *last (band size, CG
+ * iterations, volume, mass; energy fields are left at 0 -- use etd_energy). */
+etd_status etd_step(etd_plan_t plan, void *phi, void *u, int nsteps, etd_diag *last);
+
+/* Diagnostics of (phi, u): energy of Eq. (2.16) (nonlocal term by a band solve of
+ * (-Delta_{S,h}) w = g f(U) - mean), mass, bound statistics, volume.  Synchronous. */
+etd_status etd_energy(etd_plan_t plan, const void *phi, const void *u, etd_diag *out);
+
+/* Release the plan and its workspace.  etd_free(NULL) returns ETD_OK. */
+etd_status etd_free(etd_plan_t plan);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *etd_last_error(void);
+
+/* ---- Operator entry points: single rows of the step, for verification -------------- */
+
+/* Forward FFT (Sec. 3.2): real field -> half spectrum, unnormalised,
+ * out[(kz*Ny + ky)*(Nx/2+1) + kx] (complex as interleaved re,im of the element type). */
+etd_status etd_fft_forward(etd_plan_t plan, const void *field, void *half_spectrum);
+
+/* Inverse FFT: half spectrum (layout above) -> real field, with the 1/N factor.  The
+ * imaginary parts of self-conjugate modes are ignored (real-to-complex convention). */
+etd_status etd_fft_inverse(etd_plan_t plan, const void *half_spectrum, void *field);
+
+/* Narrow band of phi (Sec. 3.2): writes the ascending flat indices of the band nodes
+ * {|2 phi - 1| < band_mask_hi} to idx (device int32, capacity N) and the count to
+ * *count (host).  Synchronous. */
+etd_status etd_band(etd_plan_t plan, const void *phi, int *idx, long *count);
+
+/* Band-restricted nonlocal solve: w = (-Delta_{S,h})^{-1}(f - mean) on the band of phi
+ * with zero-flux band edges, g = g(phi) (Eq. (2.3)); f and w are full fields, w = 0
+ * off the band.  Warm start from the incoming w.  Synchronous; reports iterations and
+ * relative residual. */
+etd_status etd_nonlocal(etd_plan_t plan, const void *phi, const void *f, void *w,
+                        int *iters, double *resid);
+
+/* Nonlinear remainders as real fields:
+ *   which = 1: R1(phi, u) of the force balance (Sec. 3.1), phi_old unused;
+ *   which = 2: R2(phi, u) of the coupled OK equation with advection velocity from
+ *              (phi - phi_old)/tau (coupled plans), zero off the band;
+ *   which = 3: R2 of the fixed-membrane model with g = g(phi) (fixed plans).
+ * Synchronous. */
+etd_status etd_remainder(etd_plan_t plan, int which, const void *phi, const void *phi_old,
+                         const void *u, void *out);
+
+/* ---- Per-kernel timing (measurement support; no counterpart in the paper) ----------- */
+
+/* Kernel classes reported by etd_timing_read. */
+typedef enum {
+  ETD_K_FFT_A_FWD = 0,   /* pass A forward: x real-to-complex + inner y DFT             */
+  ETD_K_FFT_A_INV = 1,   /* pass A inverse (+ fused pointwise epilogue)                  */
+  ETD_K_FFT_B = 2,       /* pass B: outer y + z DFT, fused spectral ETD update, inverse  */
+  ETD_K_CG = 3,          /* persistent band CG (one launch per solve)                    */
+  ETD_K_POINTWISE = 4,   /* R1, R2, Delta_S u and other full-grid pointwise kernels      */
+  ETD_K_BAND = 5,        /* band compaction and CG set-up                                */
+  ETD_K_REDUCE = 6,      /* FP64 reductions                                              */
+  ETD_K_NKINDS = 7
+} etd_kernel_kind;
+
+/* enable = 1: reset the counters and bracket every later launch with CUDA events on the
+ * plan's stream; enable = 0: stop recording (counters are kept). */
+etd_status etd_timing(etd_plan_t plan, int enable);
+
+/* Totals since the last etd_timing(plan, 1) for one kernel class: summed event time
+ * (ms), launch count, and the algorithmic bytes of those launches (each real field
+ * element and each half-spectrum complex element read or written once, at the element
+ * size of the plan's precision).  Synchronises the stream. */
+etd_status etd_timing_read(etd_plan_t plan, int kind, double *total_ms, long *launches,
+                           double *algo_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ETD_H */

@@ -1,0 +1,5 @@
+// Double-precision instantiation.
+#include "stepper.cuh"
+namespace etd {
+PlanBase* make_plan_f64(const etd_params& p, cudaStream_t s) { return new Stepper<double>(p, s); }
+}  // namespace etd

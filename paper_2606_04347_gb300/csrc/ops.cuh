@@ -1,0 +1,163 @@
+// ops.cuh -- spectral operators run inside pass B on the spectrum held in shared memory.
+//
+// Coefficient table (built in FP64 on the host, Sec. 2.2 phi-functions of Sec. 3.2
+// symbols): for every integer m = |k|^2 of the cubic box, 6 entries
+//   tab[6m + 0..2] = phi0, tau phi1, tau phi2 at z = tau l^phi(lambda_m)
+//   tab[6m + 3..5] = phi0, tau phi1, tau phi2 at z = tau l^u(lambda_m)
+// with lambda_m = -(pi/X)^2 m.
+#pragma once
+#include "fft.cuh"
+
+namespace etd {
+
+template <typename T> struct SpecConst {
+  const T* tab;    // 6 coefficients per m
+  T inv_n;         // 1/(Nx Ny Nz): the inverse transform's factor
+  T kscale;        // pi / X
+  T ksq;           // (pi / X)^2
+};
+
+template <typename T, typename C>
+__device__ __forceinline__ C deriv_mult(int o, C v, const Wave& w, const SpecConst<T>& k) {
+  // o = 0: identity, 1: Laplacian (lambda), 2..4: d/dx, d/dy, d/dz (i k, Nyquist -> 0)
+  if (o == 0) return cscale(v, k.inv_n);
+  if (o == 1) return cscale(v, -k.ksq * (T)w.m * k.inv_n);
+  const int s = (o == 2) ? w.sx : (o == 3 ? w.sy : w.sz);
+  const T f = k.kscale * (T)s * k.inv_n;
+  return C{-f * v.y, f * v.x};
+}
+
+// Forward only: store the spectrum (plan layout).
+template <typename T> struct OpStore {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 1;
+  int nout;
+  C* spec;
+  __device__ void combine(int, long long ge, const Wave&, C& s0, C&) const { spec[ge] = s0; }
+  __device__ C out(int, C v, const Wave&) const { return v; }
+};
+
+// Load a stored spectrum and emit multipliers of it (identity, Laplacian, gradient).
+// `sel` lists the outputs (codes of deriv_mult).
+template <typename T> struct OpDeriv {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 0;
+  int nout;
+  int sel[5];
+  const C* spec;
+  SpecConst<T> k;
+  __device__ void combine(int, long long ge, const Wave&, C& s0, C&) const { s0 = spec[ge]; }
+  __device__ C out(int o, C v, const Wave& w) const { return deriv_mult<T>(sel[o], v, w, k); }
+};
+
+// phi-stage predictor (Sec. 3.3): R1^ = FFT(R_rest) + kappa/(mu eps^2) lambda FFT(W'-A1 phi),
+// phi~^ = phi0 phi^n^ + tau phi1 R1^.  RK2 stores S = phi~^ - tau phi2 R1^ (so that the
+// corrector is S + tau phi2 R1(phi~)^); ETD1 overwrites phi^ with phi~^.
+template <typename T> struct OpPhiPred {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 2;
+  int nout;
+  int sel[5];
+  C* spec_phi;     // phi^n^ (ETD1: overwritten with phi^{n+1}^)
+  C* spec_S;       // RK2 only
+  int rk2;
+  T c_lap;         // kappa / (mu eps_phi^2)
+  SpecConst<T> k;
+  __device__ void combine(int, long long ge, const Wave& w, C& s0, C& s1) const {
+    const T lam = -k.ksq * (T)w.m;
+    const C r1 = C{s0.x + c_lap * lam * s1.x, s0.y + c_lap * lam * s1.y};
+    const T* c = k.tab + 6 * w.m;
+    const T a0 = c[0], a1 = c[1];
+    const C v = spec_phi[ge];
+    const C pt = C{a0 * v.x + a1 * r1.x, a0 * v.y + a1 * r1.y};
+    if (rk2) {
+      const T a2 = c[2];
+      spec_S[ge] = C{pt.x - a2 * r1.x, pt.y - a2 * r1.y};
+    } else {
+      spec_phi[ge] = pt;
+    }
+    s0 = pt;
+  }
+  __device__ C out(int o, C v, const Wave& w) const { return deriv_mult<T>(sel[o], v, w, k); }
+};
+
+// phi-stage corrector: phi^{n+1}^ = S + tau phi2 R1(phi~)^ ; stored and emitted.
+template <typename T> struct OpPhiCorr {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 2;
+  int nout;
+  C* spec_phi;
+  const C* spec_S;
+  T c_lap;
+  SpecConst<T> k;
+  __device__ void combine(int, long long ge, const Wave& w, C& s0, C& s1) const {
+    const T lam = -k.ksq * (T)w.m;
+    const C r1 = C{s0.x + c_lap * lam * s1.x, s0.y + c_lap * lam * s1.y};
+    const T a2 = k.tab[6 * w.m + 2];
+    const C S = spec_S[ge];
+    const C p = C{S.x + a2 * r1.x, S.y + a2 * r1.y};
+    spec_phi[ge] = p;
+    s0 = p;
+  }
+  __device__ C out(int, C v, const Wave&) const { return cscale(v, k.inv_n); }
+};
+
+// u-stage predictor: GU~^ = phi0 FFT(G u^n) + tau phi1 R2^ ; RK2 stores S = GU~^ - tau phi2 R2^.
+template <typename T> struct OpUPred {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 2;
+  int nout;
+  C* spec_S;
+  int rk2;
+  SpecConst<T> k;
+  __device__ void combine(int, long long ge, const Wave& w, C& s0, C& s1) const {
+    const T* c = k.tab + 6 * w.m + 3;
+    const C p = C{c[0] * s0.x + c[1] * s1.x, c[0] * s0.y + c[1] * s1.y};
+    if (rk2) spec_S[ge] = C{p.x - c[2] * s1.x, p.y - c[2] * s1.y};
+    s0 = p;
+  }
+  __device__ C out(int, C v, const Wave&) const { return cscale(v, k.inv_n); }
+};
+
+// u-stage corrector: GU^{n+1}^ = S + tau phi2 R2(U~)^.
+template <typename T> struct OpUCorr {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 1;
+  int nout;
+  const C* spec_S;
+  SpecConst<T> k;
+  __device__ void combine(int, long long ge, const Wave& w, C& s0, C&) const {
+    const T b2 = k.tab[6 * w.m + 5];
+    const C S = spec_S[ge];
+    s0 = C{S.x + b2 * s0.x, S.y + b2 * s0.y};
+  }
+  __device__ C out(int, C v, const Wave&) const { return cscale(v, k.inv_n); }
+};
+
+// Standard-layout half spectrum [kz][ky][kx] in/out (operator entry points).
+template <typename T> struct OpToStd {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 1;
+  int nout;
+  C* dst;
+  int ny, nxh;
+  __device__ void combine(int, long long, const Wave& w, C& s0, C&) const {
+    dst[((long long)w.kz * ny + w.ky) * nxh + w.kx] = s0;
+  }
+  __device__ C out(int, C v, const Wave&) const { return v; }
+};
+
+template <typename T> struct OpFromStd {
+  using C = typename Cplx<T>::type;
+  static constexpr int NI = 0;
+  int nout;
+  const C* src;
+  int ny, nxh;
+  T inv_n;
+  __device__ void combine(int, long long, const Wave& w, C& s0, C&) const {
+    s0 = src[((long long)w.kz * ny + w.ky) * nxh + w.kx];
+  }
+  __device__ C out(int, C v, const Wave&) const { return cscale(v, inv_n); }
+};
+
+}  // namespace etd

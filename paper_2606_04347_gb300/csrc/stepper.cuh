@@ -1,0 +1,799 @@
+// stepper.cuh -- the plan: workspace, coefficient tables and the per-step kernel sequence
+// of Algorithm 1 (coupled model) or its frozen-membrane form (fixed model).
+#pragma once
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include "kernels.cuh"
+#include "ops.cuh"
+#include "plan.h"
+
+namespace etd {
+
+// phi_0, phi_1, phi_2 of Sec. 2.2 in FP64: Taylor series below z = 1 (the closed forms
+// cancel there), closed forms through expm1 above.
+inline void phi_functions(double z, double& p0, double& p1, double& p2) {
+  p0 = std::exp(-z);
+  if (std::fabs(z) < 1.0) {
+    double s1 = 0.0, s2 = 0.0, fac1 = 1.0, fac2 = 2.0;
+    double zk = 1.0;
+    double t1[32], t2[32];
+    for (int k = 0; k < 30; ++k) {
+      t1[k] = zk / fac1;
+      t2[k] = zk / fac2;
+      zk *= -z;
+      fac1 *= (k + 2);
+      fac2 *= (k + 3);
+    }
+    for (int k = 29; k >= 0; --k) {
+      s1 += t1[k];
+      s2 += t2[k];
+    }
+    p1 = s1;
+    p2 = s2;
+  } else {
+    const double em1 = std::expm1(-z);
+    p1 = -em1 / z;
+    p2 = (em1 + z) / (z * z);
+  }
+}
+
+template <typename T> class Stepper : public PlanBase {
+ public:
+  using C = typename Cplx<T>::type;
+
+  explicit Stepper(const etd_params& P, cudaStream_t s) : P_(P), st_(s) {
+    try {
+      init();
+    } catch (...) {
+      release();
+      throw;
+    }
+  }
+  ~Stepper() override {
+    for (auto& e : ev_) cudaEventDestroy(e);
+    release();
+  }
+
+  // ------------------------------------------------------------------ public operations
+  void step(void* phi, void* u, int nsteps, etd_diag* last) override {
+    if (nsteps < 0) throw Error(ETD_EINVAL, "nsteps < 0");
+    if (!u) throw Error(ETD_EINVAL, "u is NULL");
+    if (P_.model == ETD_MODEL_COUPLED) {
+      if (!phi) throw Error(ETD_EINVAL, "coupled model needs phi");
+      run_coupled(static_cast<T*>(phi), static_cast<T*>(u), nsteps);
+    } else {
+      run_fixed(static_cast<const T*>(phi), static_cast<T*>(u), nsteps);
+    }
+    if (last) {
+      std::memset(last, 0, sizeof(*last));
+      ETD_CUDA(cudaMemsetAsync(flag_, 0, sizeof(int), st_));
+      launch_check(static_cast<T*>(u));
+      if (phi && P_.model == ETD_MODEL_COUPLED) launch_check(static_cast<T*>(phi));
+      ETD_CUDA(cudaStreamSynchronize(st_));
+      ETD_CUDA(cudaGetLastError());
+      int h[3];
+      ETD_CUDA(cudaMemcpy(h, status_, sizeof(int), cudaMemcpyDeviceToHost));
+      ETD_CUDA(cudaMemcpy(h + 1, flag_, sizeof(int), cudaMemcpyDeviceToHost));
+      ETD_CUDA(cudaMemcpy(h + 2, count_, sizeof(int), cudaMemcpyDeviceToHost));
+      double sc[S_COUNT];
+      ETD_CUDA(cudaMemcpy(sc, scal_, sizeof(sc), cudaMemcpyDeviceToHost));
+      int it = 0;
+      double rs = 0;
+      ETD_CUDA(cudaMemcpy(&it, cg_iters_, sizeof(int), cudaMemcpyDeviceToHost));
+      ETD_CUDA(cudaMemcpy(&rs, cg_resid_, sizeof(double), cudaMemcpyDeviceToHost));
+      last->band_size = h[2];
+      last->cg_iters_last = it;
+      last->cg_resid_last = rs;
+      last->volume = hvol_ * sc[S_VOL];
+      last->mass = hvol_ * sc[S_MASS];
+      if (h[1]) throw Error(ETD_ENONFINITE, "non-finite value in the state");
+      check_status(h[0]);
+    }
+  }
+
+  void energy(const void* phi, const void* u, etd_diag* out) override {
+    if (!u || !out) throw Error(ETD_EINVAL, "u/out is NULL");
+    const T* ph = static_cast<const T*>(phi);
+    if (!ph) {
+      if (!fixed_ready_) throw Error(ETD_EINVAL, "energy needs phi");
+      ph = phiA_;
+    }
+    const T* U = static_cast<const T*>(u);
+    T* Ge = gx_;
+    T* xe = gy_;
+    launch_grid(k_gloc<T>, g_.n, ph, Ge);
+    compute_band(ph);
+    band_dirty_ = true;
+    cg_setup(Ge);
+    ETD_CUDA(cudaMemsetAsync(xe, 0, sizeof(T) * g_.n, st_));
+    cg_solve(RhsGF<T>{Ge, U}, xe);
+    ETD_CUDA(cudaMemsetAsync(scal_ + S_GRAD, 0, sizeof(double) * 5, st_));
+    double init[3] = {0.0, 1e300, -1e300};
+    ETD_CUDA(cudaMemcpyAsync(scal_ + S_MAXB, init, sizeof(init), cudaMemcpyHostToDevice, st_));
+    k_energy_terms<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, Ge, U, ph, scal_);
+    k_band_dot<T><<<nsm_ * 4, 256, 0, st_>>>(idx_, count_, xe, RhsGF<T>{Ge, U}, scal_ + S_NONLOC);
+    ETD_CUDA(cudaGetLastError());
+    ETD_CUDA(cudaStreamSynchronize(st_));
+    double sc[S_COUNT];
+    ETD_CUDA(cudaMemcpy(sc, scal_, sizeof(sc), cudaMemcpyDeviceToHost));
+    int h[2];
+    ETD_CUDA(cudaMemcpy(h, status_, sizeof(int), cudaMemcpyDeviceToHost));
+    ETD_CUDA(cudaMemcpy(h + 1, count_, sizeof(int), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    const double mass = hvol_ * sc[S_MASSF];
+    out->energy = 0.5 * P_.eps_u * hvol_ * sc[S_GRAD] + hvol_ * sc[S_WELL] / P_.eps_u +
+                  0.5 * P_.gamma * hvol_ * sc[S_NONLOC] + 0.5 * P_.M * mass * mass;
+    out->mass = mass;
+    out->max_bound = sc[S_MAXB];
+    out->umin = sc[S_UMIN];
+    out->umax = sc[S_UMAX];
+    out->volume = hvol_ * sc[S_VOLE];
+    out->band_size = h[1];
+    int it = 0;
+    double rs = 0;
+    ETD_CUDA(cudaMemcpy(&it, cg_iters_, sizeof(int), cudaMemcpyDeviceToHost));
+    ETD_CUDA(cudaMemcpy(&rs, cg_resid_, sizeof(double), cudaMemcpyDeviceToHost));
+    out->cg_iters_last = it;
+    out->cg_resid_last = rs;
+    check_status(h[0]);
+  }
+
+  void fft_forward(const void* field, void* half) override {
+    fwd(ProLoad<T>{static_cast<const T*>(field)}, I_[0]);
+    OpToStd<T> op{0, static_cast<C*>(half), g_.ny, g_.nxh};
+    passb(op, I_[0], nullptr, outs({}));
+    sync_check();
+  }
+
+  void fft_inverse(const void* half, void* field) override {
+    OpFromStd<T> op{1, static_cast<const C*>(half), g_.ny, g_.nxh, sk_.inv_n};
+    passb(op, nullptr, nullptr, outs({I_[0]}));
+    inv(I_[0], EpiStore<T>{static_cast<T*>(field)});
+    sync_check();
+  }
+
+  long band(const void* phi, int* idx) override {
+    compute_band(static_cast<const T*>(phi));
+    band_dirty_ = true;
+    int cnt = 0;
+    ETD_CUDA(cudaMemcpyAsync(&cnt, count_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    ETD_CUDA(cudaStreamSynchronize(st_));
+    if (cnt) ETD_CUDA(cudaMemcpyAsync(idx, idx_, sizeof(int) * cnt, cudaMemcpyDeviceToDevice, st_));
+    sync_check();
+    return cnt;
+  }
+
+  void nonlocal(const void* phi, const void* f, void* w, int* iters, double* resid) override {
+    T* Ge = gx_;
+    T* xe = static_cast<T*>(w);
+    launch_grid(k_gloc<T>, g_.n, static_cast<const T*>(phi), Ge);
+    compute_band(static_cast<const T*>(phi));
+    band_dirty_ = true;
+    cg_setup(Ge);
+    // the solution is defined on the band only
+    k_zero_off_band<<<grid_for(g_.n), 256, 0, st_>>>(g_.n, mask_, (void*)xe, (int)sizeof(T));
+    cg_solve(RhsField<T>{static_cast<const T*>(f)}, xe);
+    int it = 0;
+    double rs = 0;
+    ETD_CUDA(cudaMemcpyAsync(&it, cg_iters_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    ETD_CUDA(cudaMemcpyAsync(&rs, cg_resid_, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    sync_check();
+    if (iters) *iters = it;
+    if (resid) *resid = rs;
+  }
+
+  void remainder(int which, const void* phi_, const void* phio_, const void* u_, void* out_) override {
+    const T* phi = static_cast<const T*>(phi_);
+    const T* U = static_cast<const T*>(u_);
+    T* out = static_cast<T*>(out_);
+    band_dirty_ = true;
+    w_reset_ = true;
+    if (which == 1) {
+      ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
+      launch_reduce(0, phi, nullptr, scal_ + S_VOL);
+      set_a0_if_needed();
+      forward_store(phi, sS_);
+      derivs(sS_, phi);
+      phi_terms(phi, U);
+      // Delta(W' - A1 phi) spectrally, then R1 = rest + kappa/(mu eps^2) Delta(W' - A1 phi)
+      forward_store(wm_, sS_);
+      OpDeriv<T> op{1, {1, 0, 0, 0, 0}, sS_, sk_};
+      passb(op, nullptr, nullptr, outs({I_[0]}));
+      inv(I_[0], EpiStore<T>{wm_});
+      const T c = (T)(P_.kappa / (P_.mu * P_.eps_phi * P_.eps_phi));
+      launch_grid(k_axpy<T>, g_.n, (const T*)rr_, c, (const T*)wm_, out);
+    } else if (which == 2) {
+      if (P_.model != ETD_MODEL_COUPLED) throw Error(ETD_EINVAL, "which = 2 needs a coupled plan");
+      T* Ge = G_;
+      launch_grid(k_gloc<T>, g_.n, phi, Ge);
+      compute_band(phi);
+      cg_setup(Ge);
+      ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+      launch_reduce(1, U, Ge, scal_ + S_MASS);
+      ETD_CUDA(cudaMemsetAsync(w_, 0, sizeof(T) * g_.n, st_));
+      cg_solve(RhsGU<T>{Ge, U, P_.ubar}, w_);
+      k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, phi, static_cast<const T*>(phio_), U, w_, scal_,
+                                                        hvol_, out);
+    } else if (which == 3) {
+      T* Ge = G_;
+      launch_grid(k_gloc<T>, g_.n, phi, Ge);
+      compute_band(phi);
+      cg_setup(Ge);
+      ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+      launch_reduce(2, U, Ge, scal_ + S_MASS);
+      ETD_CUDA(cudaMemsetAsync(w_, 0, sizeof(T) * g_.n, st_));
+      cg_solve(RhsGF<T>{Ge, U}, w_);
+      k_r2_fixed<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, Ge, mask_, U, w_, scal_, hvol_, out);
+      fixed_ready_ = false;
+    } else {
+      throw Error(ETD_EINVAL, "which must be 1, 2 or 3");
+    }
+    sync_check();
+  }
+
+ private:
+  // ------------------------------------------------------------------ set-up
+  void init() {
+    const int nx = P_.n[0], ny = P_.n[1], nz = P_.dim == 2 ? 1 : P_.n[2];
+    int dev = 0;
+    ETD_CUDA(cudaGetDevice(&dev));
+    ETD_CUDA(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+    int optin = 0;
+    ETD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t budget = std::min<size_t>((size_t)optin, 200 * 1024);
+    g_.dim = P_.dim;
+    g_.nx = nx;
+    g_.ny = ny;
+    g_.nz = nz;
+    g_.nxh = nx / 2 + 1;
+    g_.n = (long long)nx * ny * nz;
+    g_.nhat = (long long)g_.nxh * ny * nz;
+    g_.hx = 2.0 * P_.half_len[0] / nx;
+    g_.hy = 2.0 * P_.half_len[1] / ny;
+    g_.hz = P_.dim == 2 ? 1.0 : 2.0 * P_.half_len[2] / nz;
+    hvol_ = g_.hx * g_.hy * (P_.dim == 2 ? 1.0 : g_.hz);
+    const size_t cs = sizeof(C);
+    g_.ZB = nz == 1 ? 1 : std::min(nz, cs == 8 ? 4 : 2);
+    g_.Y2 = 0;
+    for (int y2 = ny; y2 >= 2; y2 >>= 1) {
+      const int y1 = ny / y2;
+      const size_t a = 2 * (size_t)g_.ZB * y2 * g_.nxh * cs;
+      const size_t b = 3 * (size_t)y1 * nz * cs;
+      if (a <= budget && b <= budget) {
+        g_.Y2 = y2;
+        break;
+      }
+    }
+    if (!g_.Y2) throw Error(ETD_EINVAL, "grid too large for the two-pass FFT tiles");
+    g_.Y1 = ny / g_.Y2;
+    const size_t slot1 = (size_t)g_.Y1 * nz * cs;
+    g_.KB = (int)std::max<size_t>(1, std::min<size_t>((size_t)g_.nxh, (48 * 1024) / (3 * slot1)));
+    if (nz > 1) g_.KB = 1;
+    smemA_ = 2 * (size_t)g_.ZB * g_.Y2 * g_.nxh * cs;
+    smemB_ = 3 * (size_t)g_.KB * g_.Y1 * nz * cs;
+
+    // model constants in the working precision
+    mc_.eps_phi = (T)P_.eps_phi;
+    mc_.eps_u = (T)P_.eps_u;
+    mc_.mu = (T)P_.mu;
+    mc_.lambda_surf = (T)P_.lambda_surf;
+    mc_.kappa = (T)P_.kappa;
+    mc_.lambda_line = (T)P_.lambda_line;
+    mc_.M_area = (T)P_.M_area;
+    mc_.alpha = (T)P_.alpha;
+    mc_.u0 = (T)P_.u0;
+    mc_.gamma = (T)P_.gamma;
+    mc_.M = (T)P_.M;
+    mc_.ubar = (T)P_.ubar;
+    mc_.A1 = (T)P_.A1;
+    mc_.A2 = (T)P_.A2;
+    mc_.B1 = (T)P_.B1;
+    mc_.B2 = (T)P_.B2;
+    mc_.band_hi = (T)P_.band_mask_hi;
+    mc_.delta = (T)P_.recover_delta;
+    mc_.tau = (T)P_.tau;
+    const double h[3] = {g_.hx, g_.hy, g_.hz};
+    for (int d = 0; d < 3; ++d) {
+      mc_.ih2[d] = (T)(1.0 / (h[d] * h[d]));
+      mc_.i2h[d] = (T)(0.5 / h[d]);
+    }
+    mc_.dim = P_.dim;
+    mc_.linear_only = P_.linear_only;
+
+    // workspace
+    for (int i = 0; i < 5; ++i) I_[i] = alloc<C>(g_.nhat);
+    sphi_ = alloc<C>(g_.nhat);
+    sS_ = alloc<C>(g_.nhat);
+    sSu_ = alloc<C>(g_.nhat);
+    T** reals[] = {&phiA_, &phiB_, &phit_, &lap_, &gx_, &gy_, &gz_, &lu_, &rr_, &wm_, &r2_, &ut_, &G_, &w_,
+                   &cg_.r, &cg_.p, &cg_.q, &cg_.cx, &cg_.cy, &cg_.cz, &cg_.idg};
+    for (T** r : reals) *r = alloc<T>(g_.n);
+    for (T** r : reals) ETD_CUDA(cudaMemset(*r, 0, sizeof(T) * g_.n));
+    cg_.x = w_;
+    mask_ = alloc<unsigned char>(g_.n);
+    idx_ = alloc<int>(g_.n);
+    idx_old_ = alloc<int>(g_.n);
+    nblk_ = (int)((g_.n + kCompactBlock - 1) / kCompactBlock);
+    bcount_ = alloc<int>(nblk_);
+    count_ = alloc<int>(1);
+    count_old_ = alloc<int>(1);
+    ETD_CUDA(cudaMemset(count_, 0, sizeof(int)));
+    ETD_CUDA(cudaMemset(count_old_, 0, sizeof(int)));
+    scal_ = alloc<double>(S_COUNT);
+    ETD_CUDA(cudaMemset(scal_, 0, sizeof(double) * S_COUNT));
+    acc_ = alloc<double>(16);
+    bar_ = alloc<unsigned>(2);
+    status_ = alloc<int>(1);
+    flag_ = alloc<int>(1);
+    cg_iters_ = alloc<int>(1);
+    cg_resid_ = alloc<double>(1);
+    cg_work_ = alloc<unsigned long long>(1);
+    ETD_CUDA(cudaMemset(cg_work_, 0, sizeof(unsigned long long)));
+    ETD_CUDA(cudaMemset(status_, 0, sizeof(int)));
+    ETD_CUDA(cudaMemset(cg_iters_, 0, sizeof(int)));
+    ETD_CUDA(cudaMemset(cg_resid_, 0, sizeof(double)));
+
+    // twiddle tables w_N^e = exp(-2 pi i e / N) and the phi-function table, built in FP64
+    twx_ = upload_twiddles(nx);
+    twy_ = upload_twiddles(ny);
+    twz_ = upload_twiddles(nz);
+    const double ks = M_PI / P_.half_len[0];
+    const int mmax = (nx / 2) * (nx / 2) + (ny / 2) * (ny / 2) + (nz / 2) * (nz / 2);
+    std::vector<T> tab(6 * (size_t)(mmax + 1));
+    const double e2 = P_.eps_phi * P_.eps_phi;
+    for (int m = 0; m <= mmax; ++m) {
+      const double lam = -ks * ks * m;
+      const double lphi = P_.kappa / P_.mu * lam * lam -
+                          (P_.kappa * (P_.A1 + P_.A2) + P_.lambda_surf * e2) / (P_.mu * e2) * lam +
+                          (P_.kappa * P_.A1 * P_.A2 + P_.lambda_surf * P_.A1 * e2) / (P_.mu * e2 * e2);
+      const double lu = P_.B2 - P_.eps_u * P_.B1 * lam;
+      double a0, a1, a2, b0, b1, b2;
+      phi_functions(P_.tau * lphi, a0, a1, a2);
+      phi_functions(P_.tau * lu, b0, b1, b2);
+      T* t = tab.data() + 6 * (size_t)m;
+      t[0] = (T)a0;
+      t[1] = (T)(P_.tau * a1);
+      t[2] = (T)(P_.tau * a2);
+      t[3] = (T)b0;
+      t[4] = (T)(P_.tau * b1);
+      t[5] = (T)(P_.tau * b2);
+    }
+    tab_ = alloc<T>(tab.size());
+    ETD_CUDA(cudaMemcpy(tab_, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
+    sk_.tab = tab_;
+    sk_.inv_n = (T)(1.0 / (double)g_.n);
+    sk_.kscale = (T)ks;
+    sk_.ksq = (T)(ks * ks);
+    c_lap_ = (T)(P_.kappa / (P_.mu * e2));
+    a0_set_ = !std::isnan(P_.A0);
+    if (a0_set_) {
+      double a0 = P_.A0;
+      ETD_CUDA(cudaMemcpy(scal_ + S_A0, &a0, sizeof(double), cudaMemcpyHostToDevice));
+    }
+    ETD_CUDA(cudaDeviceSynchronize());
+  }
+
+  C* upload_twiddles(int n) {
+    std::vector<C> t(n);
+    for (int e = 0; e < n; ++e) {
+      const long double a = 2.0L * 3.14159265358979323846264338327950288L * e / n;
+      t[e].x = (T)cosl(a);
+      t[e].y = (T)(-sinl(a));
+    }
+    C* d = alloc<C>(n);
+    ETD_CUDA(cudaMemcpy(d, t.data(), sizeof(C) * n, cudaMemcpyHostToDevice));
+    return d;
+  }
+
+  template <typename U> U* alloc(size_t count) {
+    void* p = nullptr;
+    ETD_CUDA(cudaMalloc(&p, sizeof(U) * std::max<size_t>(count, 1)));
+    allocs_.push_back(p);
+    return static_cast<U*>(p);
+  }
+
+  void release() {
+    for (void* p : allocs_) cudaFree(p);
+    allocs_.clear();
+  }
+
+  // ------------------------------------------------------------------ launch helpers
+  int grid_for(long long n) const {
+    const long long b = (n + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(b, (long long)nsm_ * 16));
+  }
+
+  template <typename K, typename... A> void launch_grid(K k, long long n, A... a) {
+    k<<<grid_for(n), 256, 0, st_>>>(n, a...);
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  void launch_reduce(int mode, const T* a, const T* G, double* dst) {
+    timed(ETD_K_REDUCE, (mode == 0 ? 1 : 2) * fld(), [&] {
+      k_reduce<T><<<grid_for(g_.n), 256, 0, st_>>>(g_.n, mode, a, G, P_.ubar, dst);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  void launch_check(T* a) {
+    k_check_finite<T><<<grid_for(g_.n), 256, 0, st_>>>(g_.n, a, flag_);
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  static int pro_reads(const ProLoad<T>&) { return 1; }
+  static int pro_reads(const ProMul<T>&) { return 2; }
+  static int epi_fields(const EpiStore<T>&) { return 1; }
+  static int epi_fields(const EpiRecover<T>&) { return 2; }
+  static int epi_fields(const EpiPhiG<T>&) { return 2; }
+
+  template <typename Pro> void fwd(Pro pro, C* out) {
+    auto k = passA_fwd<T, Pro>;
+    set_smem((const void*)k, smemA_);
+    timed(ETD_K_FFT_A_FWD, pro_reads(pro) * fld() + spc(), [&] {
+      k<<<(g_.nz / g_.ZB) * g_.Y1, 512, smemA_, st_>>>(g_, pro, out, twx_, twy_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  template <typename Epi> void inv(const C* in, Epi epi) {
+    auto k = passA_inv<T, Epi>;
+    set_smem((const void*)k, smemA_);
+    timed(ETD_K_FFT_A_INV, spc() + epi_fields(epi) * fld(), [&] {
+      k<<<(g_.nz / g_.ZB) * g_.Y1, 512, smemA_, st_>>>(g_, in, epi, twx_, twy_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  static OutP<C> outs(std::initializer_list<C*> l) {
+    OutP<C> o;
+    for (int i = 0; i < 5; ++i) o.p[i] = nullptr;
+    int i = 0;
+    for (C* c : l) o.p[i++] = c;
+    return o;
+  }
+
+  // stored-spectrum traffic of each spectral operator (reads + writes of plan spectra)
+  static int op_extra(const OpStore<T>&) { return 1; }
+  static int op_extra(const OpDeriv<T>&) { return 1; }
+  static int op_extra(const OpPhiPred<T>& o) { return o.rk2 ? 2 : 2; }
+  static int op_extra(const OpPhiCorr<T>&) { return 2; }
+  static int op_extra(const OpUPred<T>& o) { return o.rk2 ? 1 : 0; }
+  static int op_extra(const OpUCorr<T>&) { return 1; }
+  static int op_extra(const OpToStd<T>&) { return 1; }
+  static int op_extra(const OpFromStd<T>&) { return 1; }
+
+  template <typename Op> void passb(const Op& op, const C* in0, const C* in1, OutP<C> o) {
+    auto k = passB<T, Op>;
+    set_smem((const void*)k, smemB_);
+    const int nkb = (g_.nxh + g_.KB - 1) / g_.KB;
+    timed(ETD_K_FFT_B, (Op::NI + op.nout + op_extra(op)) * spc(), [&] {
+      k<<<nkb * g_.Y2, 256, smemB_, st_>>>(g_, op, in0, in1, o, twy_, twz_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  void set_smem(const void* k, size_t bytes) {
+    if (bytes > 48 * 1024) ETD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }
+
+  void sync_check() {
+    ETD_CUDA(cudaGetLastError());
+    ETD_CUDA(cudaStreamSynchronize(st_));
+    int s = 0;
+    ETD_CUDA(cudaMemcpy(&s, status_, sizeof(int), cudaMemcpyDeviceToHost));
+    check_status(s);
+  }
+
+  void check_status(int s) {
+    if (s == 0) return;
+    ETD_CUDA(cudaMemset(status_, 0, sizeof(int)));
+    if (s == 5) throw Error(ETD_ENOTCONV, "band CG did not reach cg_rtol within cg_maxit iterations");
+    if (s == 6) throw Error(ETD_ETIMEOUT, "grid barrier of the band CG timed out");
+    throw Error(ETD_ECUDA, "device status word set");
+  }
+
+  // ------------------------------------------------------------------ building blocks
+  // Narrow band of phi: mask, ascending index list, count (device).  The previous list
+  // is kept in idx_old_ so the solution can be cleared on nodes that left the band.
+  void compute_band(const T* phi) {
+    std::swap(idx_, idx_old_);
+    std::swap(count_, count_old_);
+    timed(ETD_K_BAND, fld() + (double)g_.n, [&] {
+      k_band_count<T><<<nblk_, kCompactBlock, 0, st_>>>(g_.n, phi, mc_.band_hi, mask_, bcount_);
+    });
+    timed(ETD_K_BAND, 8.0 * nblk_, [&] { k_band_scan<<<1, 1024, 0, st_>>>(nblk_, bcount_, count_); });
+    timed(ETD_K_BAND, (double)g_.n, [&] {
+      k_band_scatter<<<nblk_, kCompactBlock, 0, st_>>>(g_.n, mask_, bcount_, idx_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  void cg_setup(const T* G) {
+    CGVec<T> v = cg_;
+    timed(ETD_K_BAND, 0.0, [&] { k_cg_setup<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, mask_, G, v); });
+    timed(ETD_K_BAND, 0.0, [&] { k_cg_diag<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, v); });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  template <typename Rhs> void cg_solve(Rhs rhs, T* x) {
+    CGVec<T> v = cg_;
+    v.x = x;
+    CGCtl c;
+    c.acc = acc_;
+    c.bar = bar_;
+    c.status = status_;
+    c.iters = cg_iters_;
+    c.resid = cg_resid_;
+    c.rtol = P_.cg_rtol;
+    c.maxit = P_.cg_maxit;
+    c.budget = 4000000000LL;
+    c.work = cg_work_;
+    ETD_CUDA(cudaMemsetAsync(acc_, 0, sizeof(double) * 16, st_));
+    ETD_CUDA(cudaMemsetAsync(bar_, 0, sizeof(unsigned) * 2, st_));
+    auto k = k_cg<T, Rhs>;
+    int per = 0;
+    ETD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, 0));
+    if (per < 1) throw Error(ETD_ECUDA, "band CG kernel cannot be resident");
+    const int grid = nsm_ * std::min(per, 4);
+    Geo g = g_;
+    ModelC<T> mc = mc_;
+    const int* idx = idx_;
+    const int* cnt = count_;
+    void* args[] = {&g, &mc, &idx, &cnt, &v, &rhs, &c};
+    timed(ETD_K_CG, 0.0, [&] { ETD_CUDA(cudaLaunchCooperativeKernel((const void*)k, grid, 256, args, 0, st_)); });
+  }
+
+  void set_a0_if_needed() {
+    if (a0_set_) return;
+    k_set_a0<<<1, 1, 0, st_>>>(scal_, hvol_);
+    ETD_CUDA(cudaGetLastError());
+    a0_set_ = true;
+  }
+
+  void forward_store(const T* field, C* spec) {
+    fwd(ProLoad<T>{field}, I_[0]);
+    OpStore<T> op{0, spec};
+    passb(op, I_[0], nullptr, outs({}));
+  }
+
+  // Delta phi and grad phi of the stored spectrum into lap_, gx_, gy_, gz_.
+  void derivs(const C* spec, const T*) {
+    const int nd = g_.nz > 1 ? 4 : 3;
+    OpDeriv<T> op{nd, {1, 2, 3, 4, 0}, spec, sk_};
+    passb(op, nullptr, nullptr, outs({I_[0], I_[1], I_[2], I_[3]}));
+    inv(I_[0], EpiStore<T>{lap_});
+    inv(I_[1], EpiStore<T>{gx_});
+    inv(I_[2], EpiStore<T>{gy_});
+    if (nd == 4) inv(I_[3], EpiStore<T>{gz_});
+  }
+
+  // R1 parts at (phi, u): rr_ = R1 without the Laplacian term, wm_ = W'(phi) - A1 phi.
+  void phi_terms(const T* phi, const T* u) {
+    timed(ETD_K_POINTWISE, 2 * fld(), [&] {
+      k_surf_lap_band<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, phi, u, lu_);
+    });
+    timed(ETD_K_POINTWISE, (g_.nz > 1 ? 9 : 8) * fld(), [&] {
+      k_r1<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, phi, lap_, gx_, gy_, gz_, u, lu_, scal_, hvol_, rr_, wm_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  void band_for_solve(const T* phi, const T* G) {
+    compute_band(phi);
+    if (w_reset_) {
+      ETD_CUDA(cudaMemsetAsync(w_, 0, sizeof(T) * g_.n, st_));
+      w_reset_ = false;
+    } else {
+      k_zero_left<<<nsm_ * 4, 256, 0, st_>>>(idx_old_, count_old_, mask_, (void*)w_, (int)sizeof(T));
+    }
+    cg_setup(G);
+  }
+
+  // ------------------------------------------------------------------ the coupled step
+  void run_coupled(T* phi, T* u, int nsteps) {
+    const bool rk2 = P_.scheme == ETD_ETDRK2;
+    ETD_CUDA(cudaMemcpyAsync(phiA_, phi, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
+    T* cur = phiA_;
+    T* nxt = phiB_;
+    forward_store(cur, sphi_);
+    ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
+    launch_reduce(0, cur, nullptr, scal_ + S_VOL);
+    set_a0_if_needed();
+    const int nd = g_.nz > 1 ? 4 : 3;
+    for (int n = 0; n < nsteps; ++n) {
+      // phi-stage predictor: R1(phi^n, u^n)
+      derivs(sphi_, cur);
+      phi_terms(cur, u);
+      fwd(ProLoad<T>{rr_}, I_[0]);
+      fwd(ProLoad<T>{wm_}, I_[1]);
+      if (rk2) {
+        OpPhiPred<T> pred{1 + nd, {0, 1, 2, 3, 4}, sphi_, sS_, 1, c_lap_, sk_};
+        passb(pred, I_[0], I_[1], outs({I_[0], I_[1], I_[2], I_[3], I_[4]}));
+        inv(I_[0], EpiStore<T>{phit_});
+        inv(I_[1], EpiStore<T>{lap_});
+        inv(I_[2], EpiStore<T>{gx_});
+        inv(I_[3], EpiStore<T>{gy_});
+        if (nd == 4) inv(I_[4], EpiStore<T>{gz_});
+        ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
+        launch_reduce(0, phit_, nullptr, scal_ + S_VOL);
+        phi_terms(phit_, u);  // R1(phi~, u^n): u frozen at u^n in the corrector (Sec. 3.3)
+        fwd(ProLoad<T>{rr_}, I_[0]);
+        fwd(ProLoad<T>{wm_}, I_[1]);
+        OpPhiCorr<T> corr{1, sphi_, sS_, c_lap_, sk_};
+        passb(corr, I_[0], I_[1], outs({I_[0]}));
+      } else {
+        OpPhiPred<T> pred{1, {0, 0, 0, 0, 0}, sphi_, sS_, 0, c_lap_, sk_};
+        passb(pred, I_[0], I_[1], outs({I_[0]}));
+      }
+      inv(I_[0], EpiPhiG<T>{nxt, G_});
+      ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double) * 2, st_));  // S_VOL, S_MASS
+      launch_reduce(0, nxt, nullptr, scal_ + S_VOL);
+      launch_reduce(1, u, G_, scal_ + S_MASS);
+      // u-stage: new g times old u (Sec. 3.3)
+      band_for_solve(nxt, G_);
+      cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_);
+      timed(ETD_K_POINTWISE, 2 * fld(), [&] {
+        k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, nxt, cur, u, w_, scal_, hvol_, r2_);
+      });
+      fwd(ProMul<T>{G_, u}, I_[0]);
+      fwd(ProLoad<T>{r2_}, I_[1]);
+      OpUPred<T> upred{1, sSu_, rk2 ? 1 : 0, sk_};
+      passb(upred, I_[0], I_[1], outs({I_[0]}));
+      if (rk2) {
+        inv(I_[0], EpiRecover<T>{ut_, G_, mc_.delta});
+        ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+        launch_reduce(1, ut_, G_, scal_ + S_MASS);
+        cg_solve(RhsGU<T>{G_, ut_, P_.ubar}, w_);
+        timed(ETD_K_POINTWISE, 2 * fld(), [&] {
+          k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, nxt, cur, ut_, w_, scal_, hvol_, r2_);
+        });
+        fwd(ProLoad<T>{r2_}, I_[0]);
+        OpUCorr<T> ucorr{1, sSu_, sk_};
+        passb(ucorr, I_[0], nullptr, outs({I_[0]}));
+      }
+      inv(I_[0], EpiRecover<T>{u, G_, mc_.delta});
+      std::swap(cur, nxt);
+    }
+    ETD_CUDA(cudaMemcpyAsync(phi, cur, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  // ------------------------------------------------------------------ the fixed step
+  void run_fixed(const T* phi, T* u, int nsteps) {
+    const bool rk2 = P_.scheme == ETD_ETDRK2;
+    if (phi) {
+      ETD_CUDA(cudaMemcpyAsync(phiA_, phi, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
+      fixed_ready_ = false;
+    }
+    if (!fixed_ready_ || band_dirty_) {
+      if (!phi && !fixed_ready_) throw Error(ETD_EINVAL, "fixed model: the first call must pass phi");
+      launch_grid(k_gloc<T>, g_.n, (const T*)phiA_, G_);
+      band_for_solve(phiA_, G_);
+      fixed_ready_ = true;
+      band_dirty_ = false;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+      ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+      launch_reduce(2, u, G_, scal_ + S_MASS);
+      cg_solve(RhsGF<T>{G_, u}, w_);
+      k_r2_fixed<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, G_, mask_, u, w_, scal_, hvol_, r2_);
+      fwd(ProMul<T>{G_, u}, I_[0]);
+      fwd(ProLoad<T>{r2_}, I_[1]);
+      OpUPred<T> upred{1, sSu_, rk2 ? 1 : 0, sk_};
+      passb(upred, I_[0], I_[1], outs({I_[0]}));
+      if (rk2) {
+        inv(I_[0], EpiRecover<T>{ut_, G_, mc_.delta});
+        ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+        launch_reduce(2, ut_, G_, scal_ + S_MASS);
+        cg_solve(RhsGF<T>{G_, ut_}, w_);
+        k_r2_fixed<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, G_, mask_, ut_, w_, scal_, hvol_, r2_);
+        fwd(ProLoad<T>{r2_}, I_[0]);
+        OpUCorr<T> ucorr{1, sSu_, sk_};
+        passb(ucorr, I_[0], nullptr, outs({I_[0]}));
+      }
+      inv(I_[0], EpiRecover<T>{u, G_, mc_.delta});
+    }
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  // ------------------------------------------------------------------ timing
+ public:
+  void timing(int enable) override {
+    if (enable) {
+      if (ev_.empty()) {
+        ev_.resize(2 * kTimedMax);
+        for (auto& e : ev_) ETD_CUDA(cudaEventCreate(&e));
+      }
+      ETD_CUDA(cudaStreamSynchronize(st_));
+      recs_.clear();
+      for (int k = 0; k < ETD_K_NKINDS; ++k) {
+        t_ms_[k] = 0;
+        t_bytes_[k] = 0;
+        t_n_[k] = 0;
+        t_timed_[k] = 0;
+      }
+      ETD_CUDA(cudaMemset(cg_work_, 0, sizeof(unsigned long long)));
+    }
+    timing_ = enable != 0;
+  }
+
+  void timing_read(int kind, double* ms, long* launches, double* bytes) override {
+    ETD_CUDA(cudaStreamSynchronize(st_));
+    for (const Rec& r : recs_) {
+      float t = 0;
+      ETD_CUDA(cudaEventElapsedTime(&t, ev_[2 * r.slot], ev_[2 * r.slot + 1]));
+      t_ms_[r.kind] += t;
+      ++t_timed_[r.kind];
+    }
+    recs_.clear();
+    unsigned long long work = 0;
+    ETD_CUDA(cudaMemcpy(&work, cg_work_, sizeof(work), cudaMemcpyDeviceToHost));
+    *ms = t_ms_[kind];
+    *launches = t_n_[kind];
+    // band CG: 16 element accesses per band node and iteration (stencil on p; x, r, p, q,
+    // inverse diagonal and three face coefficients), counted from the device work counter
+    *bytes = kind == ETD_K_CG ? 16.0 * sizeof(T) * (double)work : t_bytes_[kind];
+  }
+
+ private:
+  static constexpr int kTimedMax = 16384;
+  struct Rec {
+    int slot, kind;
+  };
+  template <typename F> void timed(int kind, double bytes, F&& launch) {
+    if (!timing_) {
+      launch();
+      return;
+    }
+    ++t_n_[kind];
+    t_bytes_[kind] += bytes;
+    const int slot = (int)(slot_next_ % kTimedMax);
+    const bool rec = (int)recs_.size() < kTimedMax;
+    if (rec) ETD_CUDA(cudaEventRecord(ev_[2 * slot], st_));
+    launch();
+    if (rec) {
+      ETD_CUDA(cudaEventRecord(ev_[2 * slot + 1], st_));
+      recs_.push_back(Rec{slot, kind});
+      ++slot_next_;
+    }
+  }
+  double fld() const { return (double)g_.n * sizeof(T); }        // one real field
+  double spc() const { return (double)g_.nhat * sizeof(C); }     // one half spectrum
+  bool timing_ = false;
+  std::vector<cudaEvent_t> ev_;
+  std::vector<Rec> recs_;
+  size_t slot_next_ = 0;
+  double t_ms_[ETD_K_NKINDS] = {}, t_bytes_[ETD_K_NKINDS] = {};
+  long t_n_[ETD_K_NKINDS] = {}, t_timed_[ETD_K_NKINDS] = {};
+  unsigned long long* cg_work_ = nullptr;
+
+  // ------------------------------------------------------------------ state
+  etd_params P_;
+  cudaStream_t st_;
+  Geo g_{};
+  ModelC<T> mc_{};
+  SpecConst<T> sk_{};
+  T c_lap_{};
+  double hvol_ = 1.0;
+  int nsm_ = 1;
+  size_t smemA_ = 0, smemB_ = 0;
+  std::vector<void*> allocs_;
+  C* I_[5] = {};
+  C *sphi_ = nullptr, *sS_ = nullptr, *sSu_ = nullptr;
+  T *phiA_ = nullptr, *phiB_ = nullptr, *phit_ = nullptr, *lap_ = nullptr, *gx_ = nullptr, *gy_ = nullptr,
+    *gz_ = nullptr, *lu_ = nullptr, *rr_ = nullptr, *wm_ = nullptr, *r2_ = nullptr, *ut_ = nullptr, *G_ = nullptr,
+    *w_ = nullptr;
+  CGVec<T> cg_{};
+  unsigned char* mask_ = nullptr;
+  int *idx_ = nullptr, *idx_old_ = nullptr, *bcount_ = nullptr, *count_ = nullptr, *count_old_ = nullptr;
+  int nblk_ = 0;
+  T* tab_ = nullptr;
+  C *twx_ = nullptr, *twy_ = nullptr, *twz_ = nullptr;
+  double *scal_ = nullptr, *acc_ = nullptr, *cg_resid_ = nullptr;
+  unsigned* bar_ = nullptr;
+  int *status_ = nullptr, *flag_ = nullptr, *cg_iters_ = nullptr;
+  bool a0_set_ = false, fixed_ready_ = false, band_dirty_ = false, w_reset_ = true;
+};
+
+}  // namespace etd
