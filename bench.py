@@ -20,7 +20,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import shutil
 import statistics
@@ -59,6 +58,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def allreduce_max(x: float, world: int) -> float:
+    """Max over ranks (identity for one rank).  Works with the nccl and gloo backends."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    devc = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=devc)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(world: int, points: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput in Mpoint-steps/s: units all replicas processed / slowest time."""
+    return world * points * steps / (ms_max / 1e3) / 1e6
 
 
 def peaks():
@@ -209,11 +225,8 @@ def run_ours(a):
     clocks = clk.stop()
     kt = plan.timing_read()
     plan.timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * npts * a.steps / (ms / 1e3) / 1e6
+    ms = allreduce_max(ms, world)
+    value = aggregate(world, npts, a.steps, ms)
     d = plan.step(phi, u, 0, diag=True)
 
     # dominant kernel class and its roofline
@@ -241,11 +254,8 @@ def run_ours(a):
         torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = world * npts * a.e2e_steps / t_e2e / 1e6
+    t_e2e = allreduce_max(t_e2e, world)
+    e2e = aggregate(world, npts, a.e2e_steps, 1e3 * t_e2e)
 
     line = None
     if rank == 0:
