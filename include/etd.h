@@ -162,6 +162,33 @@ etd_status etd_timing(etd_plan_t plan, int enable);
 etd_status etd_timing_read(etd_plan_t plan, int kind, double *total_ms, long *launches,
                            double *algo_bytes);
 
+/* ---- Forward FFT that allocates nothing ------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that may not
+ * allocate device memory -- a host application that owns all device memory through its
+ * own pool or a fixed footprint, or a latency-critical path on which cudaMalloc/cudaFree
+ * could synchronise the device.  Such callers cannot create a plan (etd_plan allocates).
+ *
+ * Same transform and output layout as etd_fft_forward: real field (dim = 2: Ny x Nx,
+ * dim = 3: Nz x Ny x Nx, x fastest) -> unnormalised half spectrum
+ * out[(kz*Ny + ky)*(Nx/2+1) + kx]; double/complex double for ETD_FP64, float/complex
+ * float for ETD_FP32_MIXED.  `field` and `half_spectrum` are caller-owned device
+ * pointers; the work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy) and
+ * the call returns after the launches.
+ *
+ * Scratch: a file-scope device array of ETD_STATIC_SCRATCH_BYTES = 8 MiB, held by every
+ * GPU that loads the library until the process exits.  The intermediate spectrum
+ * ((Nx/2+1)*Ny*Nz complex elements) plus the three twiddle tables must fit, each rounded
+ * up to 256 bytes; larger grids return ETD_EINVAL with the sizes in etd_last_error().
+ * Every call on a device shares that array and overwrites it (nothing in it needs to
+ * start at zero: the intermediate and the twiddles are fully rewritten by each call), so
+ * calls whose work overlaps on the GPU -- for example on two streams -- race; order them.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Sizes: Nx, Ny powers of two in [8, 256]; Nz = 1 (dim 2) or a power of two in [8, 256]. */
+etd_status etd_fft_forward_noalloc(int dim, const int *n, int precision, const void *field,
+                                   void *half_spectrum, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

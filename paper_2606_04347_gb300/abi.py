@@ -69,6 +69,9 @@ SIGNATURES = {
                                    ct.POINTER(ct.c_double)]),
 }
 
+SIGNATURES["etd_fft_forward_noalloc"] = (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.c_int, ct.c_void_p,
+                                                  ct.c_void_p, ct.c_void_p])
+
 KERNEL_KINDS = ["fft_a_fwd", "fft_a_inv", "fft_b", "cg", "pointwise", "band", "reduce"]
 
 

@@ -60,6 +60,11 @@ template <typename F> etd_status guard(F&& f) {
 }
 }  // namespace
 
+namespace etd {
+// Lets other translation units of the library report through etd_last_error().
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace etd
+
 extern "C" {
 
 etd_status etd_plan(const etd_params* params, void* cuda_stream, etd_plan_t* out) {
