@@ -42,6 +42,7 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 // Grid geometry and the four-step split, passed by value to every kernel.
 struct Geo {
   int dim, nx, ny, nz, nxh;
+  int lx, ly;          // log2 nx, log2 ny (neighbour arithmetic of the pointwise kernels)
   int Y1, Y2, ZB, KB;
   long long n, nhat;
   double hx, hy, hz;

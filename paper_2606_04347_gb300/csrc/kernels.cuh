@@ -70,30 +70,27 @@ __device__ __forceinline__ void atomic_max_d(double* dst, double v) {
   } while (assumed != old);
 }
 
-// Periodic neighbours of flat index p.
+// Periodic neighbours of flat index p (power-of-two extents: shifts and masks only).
 struct Nb {
-  long long c, xm, xp, ym, yp, zm, zp;
+  int c, xm, xp, ym, yp, zm, zp;
 };
-__device__ __forceinline__ Nb neighbours(const Geo& g, long long p) {
-  const int x = (int)(p % g.nx);
-  const long long t = p / g.nx;
-  const int y = (int)(t % g.ny);
-  const int z = (int)(t / g.ny);
-  const long long row = p - x;
-  const long long pl = (long long)g.nx * g.ny;
-  const long long plane = p - (long long)y * g.nx - x;
+__device__ __forceinline__ Nb neighbours(const Geo& g, int p) {
+  const int mx = g.nx - 1, my = g.ny - 1, mz = g.nz - 1;
+  const int sp = g.lx + g.ly;
+  const int x = p & mx;
+  const int y = (p >> g.lx) & my;
+  const int z = p >> sp;
+  const int rowbase = p - x;
+  const int inplane = p & ((1 << sp) - 1);
+  const int planebase = p - inplane;
   Nb n;
   n.c = p;
-  n.xm = row + (x == 0 ? g.nx - 1 : x - 1);
-  n.xp = row + (x == g.nx - 1 ? 0 : x + 1);
-  n.ym = plane + (long long)(y == 0 ? g.ny - 1 : y - 1) * g.nx + x;
-  n.yp = plane + (long long)(y == g.ny - 1 ? 0 : y + 1) * g.nx + x;
-  if (g.nz > 1) {
-    n.zm = (long long)(z == 0 ? g.nz - 1 : z - 1) * pl + (p - (long long)z * pl);
-    n.zp = (long long)(z == g.nz - 1 ? 0 : z + 1) * pl + (p - (long long)z * pl);
-  } else {
-    n.zm = n.zp = p;
-  }
+  n.xm = rowbase + ((x - 1) & mx);
+  n.xp = rowbase + ((x + 1) & mx);
+  n.ym = planebase + ((((y - 1) & my)) << g.lx) + x;
+  n.yp = planebase + ((((y + 1) & my)) << g.lx) + x;
+  n.zm = (((z - 1) & mz) << sp) + inplane;
+  n.zp = (((z + 1) & mz) << sp) + inplane;
   return n;
 }
 
@@ -165,7 +162,7 @@ template <typename T> struct EpiPhiG {
 template <typename T>
 __global__ void k_surf_lap_band(Geo g, ModelC<T> mc, const T* __restrict__ phi, const T* __restrict__ u,
                                 T* __restrict__ out) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n; p += (long long)gridDim.x * blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
     const T f = phi[p];
     if (!in_band(f, mc.band_hi)) {
       out[p] = 0;
@@ -190,7 +187,7 @@ __global__ void k_r1(Geo g, ModelC<T> mc, const T* __restrict__ phi, const T* __
   const T c_a = mc.kappa / (mc.mu * e2);
   const T c_b = mc.kappa / (mc.mu * e2 * e2);
   const T c_c = mc.lambda_surf / (mc.mu * e2);
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n; p += (long long)gridDim.x * blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
     if (mc.linear_only) {
       out_rest[p] = 0;
       out_wm[p] = 0;
@@ -215,7 +212,7 @@ __global__ void k_r1(Geo g, ModelC<T> mc, const T* __restrict__ phi, const T* __
 // Membrane-velocity flux component d of g u v at q: v = -d_t phi grad phi / (|grad phi|^2 + 1e-12).
 template <typename T>
 __device__ __forceinline__ void adv_flux(const Geo& g, const ModelC<T>& mc, const T* __restrict__ phin,
-                                         const T* __restrict__ phio, const T* __restrict__ u, long long q,
+                                         const T* __restrict__ phio, const T* __restrict__ u, int q,
                                          T& Fx, T& Fy, T& Fz) {
   const Nb n = neighbours(g, q);
   const T px = (phin[n.xp] - phin[n.xm]) * mc.i2h[0];
@@ -236,7 +233,7 @@ __global__ void k_r2_coupled(Geo g, ModelC<T> mc, const T* __restrict__ phin, co
                              const T* __restrict__ u, const T* __restrict__ w, const double* __restrict__ scal,
                              double hvol, T* __restrict__ out) {
   const T mass = (T)(hvol * scal[S_MASS]);
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n; p += (long long)gridDim.x * blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
     const T f = phin[p];
     if (mc.linear_only || !in_band(f, mc.band_hi)) {
       out[p] = 0;
@@ -276,7 +273,7 @@ __global__ void k_r2_fixed(Geo g, ModelC<T> mc, const T* __restrict__ G, const u
                            const T* __restrict__ u, const T* __restrict__ w, const double* __restrict__ scal,
                            double hvol, T* __restrict__ out) {
   const T mass = (T)(hvol * scal[S_MASS]);
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n; p += (long long)gridDim.x * blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
     if (mc.linear_only || !mask[p]) {
       out[p] = 0;
       continue;
@@ -339,7 +336,7 @@ __global__ void k_energy_terms(Geo g, ModelC<T> mc, const T* __restrict__ G, con
                                const T* __restrict__ phi, double* scal) {
   double sg = 0, sw = 0, sm = 0, sv = 0;
   double mb = 0, mn = 1e300, mx = -1e300;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n; p += (long long)gridDim.x * blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
     const Nb n = neighbours(g, p);
     const double gc = G[p], uc = U[p];
     const double dx = (double)U[n.xp] - uc, dy = (double)U[n.yp] - uc;
@@ -396,6 +393,22 @@ __global__ void k_band_count(long long n, const T* __restrict__ phi, T hi, unsig
   }
 }
 
+// Block counts of a uint8 mask (same blocking as k_band_count).
+static __global__ void k_mask_count(long long n, const unsigned char* __restrict__ mask, int* __restrict__ bcount) {
+  const long long p = blockIdx.x * (long long)kCompactBlock + threadIdx.x;
+  const bool b = (p < n) && mask[p];
+  const unsigned bal = __ballot_sync(0xffffffffu, b);
+  __shared__ int wc[32];
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = wc[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = v;
+  }
+}
+
 // Exclusive scan of nb block counts in place (single block); total -> *count.
 static __global__ void k_band_scan(int nb, int* __restrict__ bcount, int* __restrict__ count) {
   __shared__ int part[1024];
@@ -421,7 +434,7 @@ static __global__ void k_band_scan(int nb, int* __restrict__ bcount, int* __rest
 }
 
 static __global__ void k_band_scatter(long long n, const unsigned char* __restrict__ mask, const int* __restrict__ boff,
-                               int* __restrict__ idx) {
+                               int* __restrict__ idx, int* __restrict__ bmap) {
   const long long p = blockIdx.x * (long long)kCompactBlock + threadIdx.x;
   const bool b = (p < n) && mask[p];
   const unsigned bal = __ballot_sync(0xffffffffu, b);
@@ -440,45 +453,51 @@ static __global__ void k_band_scatter(long long n, const unsigned char* __restri
     wc[lane] = inc - v;
   }
   __syncthreads();
-  if (b) idx[boff[blockIdx.x] + wc[wid] + __popc(bal & ((1u << lane) - 1u))] = (int)p;
+  if (b) {
+    const int i = boff[blockIdx.x] + wc[wid] + __popc(bal & ((1u << lane) - 1u));
+    idx[i] = (int)p;
+    bmap[p] = i;
+  }
 }
 
 // ---- band CG for (-Delta_{S,h}) w = f - mean on the band ---------------------------------
-// Face coefficients c_d(p) = (G_p + G_{p+e_d})/2 when p and p+e_d are both band nodes, else 0
-// (zero flux across the band edge).  Vectors live in full-grid layout, band entries only.
+// The band operator in compact form: for band node i (grid point p = idx[i]) and each of its
+// 2d faces, c = (G_p + G_q)/(2 h^2) when the neighbour q is also a band node, else 0 (zero
+// flux across the band edge); (A v)_i = sum_faces c (v_i - v_q).  Vectors are compact
+// (length M, band order), so every CG phase streams contiguous arrays.
 template <typename T> struct CGVec {
-  T *x, *r, *p, *q, *cx, *cy, *cz, *idg;
+  T *x, *r, *u, *p, *q;   // compact vectors; q holds s = A p
+  T* idg;                 // inverse diagonal
+  T* c;                   // face coefficients, c[d * cap + i], d = x+, x-, y+, y-, z+, z-
+  int* nb;                // compact index of the face neighbour (i itself when absent)
+  int cap;
 };
 
 template <typename T>
 __global__ void k_cg_setup(Geo g, ModelC<T> mc, const int* __restrict__ idx, const int* __restrict__ count,
-                           const unsigned char* __restrict__ mask, const T* __restrict__ G, CGVec<T> v) {
+                           const unsigned char* __restrict__ mask, const int* __restrict__ bmap,
+                           const T* __restrict__ G, CGVec<T> v) {
   const int M = *count;
+  const int nd = g.nz > 1 ? 6 : 4;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const long long p = idx[i];
+    const int p = idx[i];
     const Nb n = neighbours(g, p);
+    const int q[6] = {n.xp, n.xm, n.yp, n.ym, n.zp, n.zm};
     const T gc = G[p];
-    v.cx[p] = mask[n.xp] ? (T)0.5 * (gc + G[n.xp]) : (T)0;
-    v.cy[p] = mask[n.yp] ? (T)0.5 * (gc + G[n.yp]) : (T)0;
-    if (!mask[n.xm]) v.cx[n.xm] = 0;
-    if (!mask[n.ym]) v.cy[n.ym] = 0;
-    if (g.nz > 1) {
-      v.cz[p] = mask[n.zp] ? (T)0.5 * (gc + G[n.zp]) : (T)0;
-      if (!mask[n.zm]) v.cz[n.zm] = 0;
+    T d = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      T c = 0;
+      int j = i;
+      if (f < nd && mask[q[f]]) {
+        c = (T)0.5 * (gc + G[q[f]]) * mc.ih2[f >> 1];
+        j = bmap[q[f]];
+      }
+      v.c[f * v.cap + i] = c;
+      v.nb[f * v.cap + i] = j;
+      d += c;
     }
-  }
-}
-
-template <typename T>
-__global__ void k_cg_diag(Geo g, ModelC<T> mc, const int* __restrict__ idx, const int* __restrict__ count,
-                          CGVec<T> v) {
-  const int M = *count;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const long long p = idx[i];
-    const Nb n = neighbours(g, p);
-    T d = (v.cx[p] + v.cx[n.xm]) * mc.ih2[0] + (v.cy[p] + v.cy[n.ym]) * mc.ih2[1];
-    if (g.nz > 1) d += (v.cz[p] + v.cz[n.zm]) * mc.ih2[2];
-    v.idg[p] = d > (T)0 ? (T)1 / d : (T)1;
+    v.idg[i] = d > (T)0 ? (T)1 / d : (T)1;
   }
 }
 
@@ -496,14 +515,12 @@ static __global__ void k_zero_left(const int* __restrict__ old_idx, const int* _
 }
 
 template <typename T>
-__device__ __forceinline__ T neg_lap_apply(const Geo& g, const ModelC<T>& mc, const CGVec<T>& v, const T* __restrict__ a,
-                                           long long p) {
-  const Nb n = neighbours(g, p);
-  const T ac = a[p];
-  T s = (v.cx[p] * (a[n.xp] - ac) - v.cx[n.xm] * (ac - a[n.xm])) * mc.ih2[0] +
-        (v.cy[p] * (a[n.yp] - ac) - v.cy[n.ym] * (ac - a[n.ym])) * mc.ih2[1];
-  if (g.nz > 1) s += (v.cz[p] * (a[n.zp] - ac) - v.cz[n.zm] * (ac - a[n.zm])) * mc.ih2[2];
-  return -s;
+__device__ __forceinline__ T band_apply(const CGVec<T>& v, const T* __restrict__ a, int i) {
+  const T ai = a[i];
+  T s = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) s += v.c[f * v.cap + i] * (ai - a[v.nb[f * v.cap + i]]);
+  return s;
 }
 
 // Right-hand sides f of the band solve.
@@ -557,7 +574,7 @@ __device__ __forceinline__ bool grid_sync(const CGCtl& c) {
           atomicCAS(c.status, 0, 6);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -567,11 +584,240 @@ __device__ __forceinline__ bool grid_sync(const CGCtl& c) {
   return ok;
 }
 
-enum { A_SUMF = 0, A_BB = 1, A_RZ0 = 2, A_RR0 = 3, A_PQ = 4, A_RZ = 6, A_RR = 8, A_SUMX = 10 };
+// ---- aggregation multigrid preconditioner for the band CG ---------------------------------
+// Level l lives on the grid coarsened 2x per axis l times (z only in 3D); its nodes are the
+// cells that contain at least one node of level l-1 (an aggregate of up to 2x2x2 nodes).
+// With piecewise-constant prolongation P the Galerkin operator P^T A P of a graph Laplacian
+// is again a graph Laplacian whose coupling between two neighbouring aggregates is the sum
+// of the fine couplings crossing between them, so every level keeps the 7-point compact
+// form (c, nb, inverse diagonal).  The preconditioner is one symmetric V(1,1) cycle with
+// weighted Jacobi (omega) and an even number of Jacobi sweeps on the coarsest level.
+constexpr int kMGMax = 7;
 
+template <typename T> struct MGL {
+  const int* cnt;      // node count (device)
+  const int* list;     // flat cell index of each node on this level's grid
+  const T* c;          // couplings c[f * cap + i]
+  const int* nb;       // neighbour node of each face (i itself when absent)
+  const T* idg;        // inverse diagonal
+  int cap;
+  const int* agg;      // parent node on level l+1 (l < nlev-1)
+  const int* child;    // child[k * cap + I]: node of level l-1 in sub-cell k, -1 if none (l >= 1)
+  T* b;                // right-hand side (level 0: the CG residual r)
+  T* e;                // pre-smoothed correction
+  T* o;                // output correction (level 0: the preconditioned residual u)
+};
+
+template <typename T> struct MGP {
+  int nlev;            // 1 = plain Jacobi
+  int gl;              // levels 0..gl-1 are processed by the whole grid, the rest by block 0
+  int csweeps;         // Jacobi sweeps on the coarsest level (even)
+  T omega;
+  MGL<T> L[kMGMax];
+};
+
+// mark the cells of level l (grid lxc, lyc) holding nodes of level l-1 (grid lxf, lyf)
+static __global__ void k_mg_mark(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
+                                 int is3d, int lxc, int lyc, unsigned char* __restrict__ mark) {
+  const int M = *cnt;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int p = list[i];
+    const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
+    const int C = (((is3d ? Z >> 1 : 0) << (lxc + lyc)) | ((Y >> 1) << lxc) | (X >> 1));
+    mark[C] = 1;
+  }
+}
+
+static __global__ void k_mg_parent(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
+                                   int is3d, int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg) {
+  const int M = *cnt;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int p = list[i];
+    const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
+    agg[i] = cmap[((is3d ? Z >> 1 : 0) << (lxc + lyc)) | ((Y >> 1) << lxc) | (X >> 1)];
+  }
+}
+
+// Galerkin couplings of level l from level l-1.
+template <typename T>
+__global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict__ ccnt, int lxc, int lyc, int lzc,
+                            int is3d, const unsigned char* __restrict__ fmark, const int* __restrict__ fmap,
+                            int lxf, int lyf, const T* __restrict__ fc, int fcap, const int* __restrict__ cmap,
+                            T* __restrict__ c, int* __restrict__ nb, T* __restrict__ idg, int* __restrict__ child,
+                            int cap) {
+  const int M = *ccnt;
+  const int mx = (1 << lxc) - 1, my = (1 << lyc) - 1, mz = (1 << lzc) - 1;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < M; I += gridDim.x * blockDim.x) {
+    const int C = clist[I];
+    const int X = C & mx, Y = (C >> lxc) & my, Z = C >> (lxc + lyc);
+    T s[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 8; ++k) {
+      const int a = k & 1, b = (k >> 1) & 1, cz = k >> 2;
+      int j = -1;
+      if (is3d || cz == 0) {
+        const int F = (((2 * Z + cz) << (lxf + lyf)) | ((2 * Y + b) << lxf) | (2 * X + a));
+        if (fmark[F]) j = fmap[F];
+      }
+      child[k * cap + I] = j;
+      if (j < 0) continue;
+      s[a ? 0 : 1] += fc[(a ? 0 : 1) * fcap + j];
+      s[b ? 2 : 3] += fc[(b ? 2 : 3) * fcap + j];
+      if (is3d) s[cz ? 4 : 5] += fc[(cz ? 4 : 5) * fcap + j];
+    }
+    const int ncell[6] = {(Z << (lxc + lyc)) | (Y << lxc) | ((X + 1) & mx), (Z << (lxc + lyc)) | (Y << lxc) | ((X - 1) & mx),
+                          (Z << (lxc + lyc)) | (((Y + 1) & my) << lxc) | X, (Z << (lxc + lyc)) | (((Y - 1) & my) << lxc) | X,
+                          (((Z + 1) & mz) << (lxc + lyc)) | (Y << lxc) | X, (((Z - 1) & mz) << (lxc + lyc)) | (Y << lxc) | X};
+    T d = 0;
+    for (int f = 0; f < 6; ++f) {
+      c[f * cap + I] = s[f];
+      nb[f * cap + I] = s[f] > (T)0 ? cmap[ncell[f]] : I;
+      d += s[f];
+    }
+    idg[I] = d > (T)0 ? (T)1 / d : (T)1;
+  }
+}
+
+template <typename T> __device__ __forceinline__ T mg_apply(const MGL<T>& L, const T* __restrict__ v, int i) {
+  const T vi = v[i];
+  T s = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) s += L.c[f * L.cap + i] * (vi - v[L.nb[f * L.cap + i]]);
+  return s;
+}
+
+// Barrier between consecutive V-cycle phases: a grid barrier when either phase runs on the
+// whole grid, a block barrier inside block 0 when both run on block 0 alone.  The first
+// call is free: the caller has already synchronised the grid.
+struct PhaseSync {
+  bool prev, first;
+  __device__ bool step(bool cur, const CGCtl& c) {
+    const bool g = prev || cur;
+    prev = cur;
+    if (first) {
+      first = false;
+      return true;
+    }
+    if (g) return grid_sync(c);
+    if (blockIdx.x == 0) __syncthreads();
+    return true;
+  }
+};
+
+// u = V(r), one symmetric V(1,1) cycle.  On entry r (level-0 b) is complete and visible;
+// on return every block has written its share of u (level-0 o) and added its part of (r,u)
+// to *ru.  Returns false when a barrier failed.
+template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c, double* ru) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  PhaseSync ps{true, true};
+  const T om = mg.omega;
+  for (int l = 0; l < mg.nlev - 1; ++l) {
+    const MGL<T>& L = mg.L[l];
+    bool grid = l < mg.gl;
+    if (!ps.step(grid, c)) return false;
+    // pre-smoothing from zero, e = omega D^{-1} b, and the residual b - A e, which needs
+    // only b at the neighbours (complete before this phase); the residual is parked in o
+    if (grid || blockIdx.x == 0) {
+      const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x, M = *L.cnt;
+      for (int i = t0; i < M; i += ns) {
+        const T ei = om * L.idg[i] * L.b[i];
+        T s = 0;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          const int j = L.nb[f * L.cap + i];
+          s += L.c[f * L.cap + i] * (ei - om * L.idg[j] * L.b[j]);
+        }
+        L.e[i] = ei;
+        L.o[i] = L.b[i] - s;
+      }
+    }
+    // restriction: sum of the children's residuals
+    const MGL<T>& Cl = mg.L[l + 1];
+    grid = (l + 1) < mg.gl;
+    if (!ps.step(grid, c)) return false;
+    if (grid || blockIdx.x == 0) {
+      const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x, M = *Cl.cnt;
+      for (int I = t0; I < M; I += ns) {
+        T s = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = Cl.child[q * Cl.cap + I];
+          if (j >= 0) s += L.o[j];
+        }
+        Cl.b[I] = s;
+      }
+    }
+  }
+  {
+    const MGL<T>& L = mg.L[mg.nlev - 1];
+    const bool grid = (mg.nlev - 1) < mg.gl;
+    const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
+    if (!ps.step(grid, c)) return false;
+    if (grid || blockIdx.x == 0) {
+      const int M = *L.cnt;
+      for (int i = t0; i < M; i += ns) L.e[i] = om * L.idg[i] * L.b[i];
+    }
+    for (int s = 1; s < mg.csweeps; ++s) {
+      if (!ps.step(grid, c)) return false;
+      const T* src = (s & 1) ? L.e : L.o;
+      T* dst = (s & 1) ? L.o : L.e;
+      if (grid || blockIdx.x == 0) {
+        const int M = *L.cnt;
+        for (int i = t0; i < M; i += ns) dst[i] = src[i] + om * L.idg[i] * (L.b[i] - mg_apply(L, src, i));
+      }
+    }
+  }
+  for (int l = mg.nlev - 2; l >= 0; --l) {
+    const MGL<T>& L = mg.L[l];
+    const MGL<T>& Cl = mg.L[l + 1];
+    const bool grid = l < mg.gl;
+    if (!ps.step(grid, c)) return false;
+    double acc = 0;
+    if (grid || blockIdx.x == 0) {
+      const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x, M = *L.cnt;
+      for (int i = t0; i < M; i += ns) {
+        const T ei = L.e[i] + Cl.o[L.agg[i]];
+        T s = 0;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          const int j = L.nb[f * L.cap + i];
+          s += L.c[f * L.cap + i] * (ei - (L.e[j] + Cl.o[L.agg[j]]));
+        }
+        const T out = ei + om * L.idg[i] * (L.b[i] - s);
+        L.o[i] = out;
+        if (l == 0) acc += (double)L.b[i] * (double)out;
+      }
+    }
+    if (l == 0) block_add(acc, ru);
+  }
+  return true;
+}
+
+enum { A_SUMF = 0, A_BB = 1, A_RU0 = 2, A_RR0 = 3, A_DU0 = 4, A_RU = 5, A_RR = 7, A_DU = 9, A_SUMX = 11 };
+
+// u = M^{-1} r with M = Jacobi (one level) or one multigrid V-cycle; adds (r,u) to *ru.
+template <typename T>
+__device__ __forceinline__ bool precond(const CGVec<T>& v, const MGP<T>& mg, const CGCtl& c, int M, double* ru) {
+  if (mg.nlev > 1) return mg_vcycle(mg, c, ru);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  double acc = 0;
+  for (int i = tid; i < M; i += nth) {
+    const T u = v.r[i] * v.idg[i];
+    v.u[i] = u;
+    acc += (double)v.r[i] * (double)u;
+  }
+  block_add(acc, ru);
+  return true;
+}
+
+// Preconditioned conjugate gradients, Chronopoulos-Gear arrangement (the recurrence
+// s = A p replaces the second matrix product of textbook CG):
+//   A: x += a p, r -= a s, rr = (r,r)                 | barrier
+//   u = M^{-1} r, gamma = (r,u)                       | barrier
+//   B: w = A u, p = u + b p, s = w + b s, delta=(w,u) | barrier
+//   b = gamma/gamma_old, a = gamma/(delta - b gamma/a_old)
 template <typename T, typename Rhs>
-__global__ void __launch_bounds__(256) k_cg(Geo g, ModelC<T> mc, const int* __restrict__ idx,
-                                            const int* __restrict__ count, CGVec<T> v, Rhs rhs, CGCtl c) {
+__global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, const int* __restrict__ count,
+                                                CGVec<T> v, T* __restrict__ wfull, Rhs rhs, CGCtl c, MGP<T> mg) {
   const int M = *count;
   if (M == 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -582,93 +828,104 @@ __global__ void __launch_bounds__(256) k_cg(Geo g, ModelC<T> mc, const int* __re
   }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   double s = 0;
-  for (int i = tid; i < M; i += nth) s += rhs(idx[i]);
+  for (int i = tid; i < M; i += nth) {
+    const int p = idx[i];
+    v.x[i] = wfull[p];          // warm start from the previous solution
+    s += rhs(p);
+  }
   block_add(s, c.acc + A_SUMF);
   if (!grid_sync(c)) return;
   const double meanf = *(volatile double*)(c.acc + A_SUMF) / M;
-  double bb = 0, rz = 0, rr = 0;
+  double bb = 0, rr = 0;
   for (int i = tid; i < M; i += nth) {
-    const long long p = idx[i];
-    const double b = rhs(p) - meanf;
-    const T r = (T)(b - (double)neg_lap_apply(g, mc, v, v.x, p));
-    const T z = r * v.idg[p];
-    v.r[p] = r;
-    v.p[p] = z;
+    const double b = rhs(idx[i]) - meanf;
+    const T r = (T)(b - (double)band_apply(v, v.x, i));
+    v.r[i] = r;
     bb += b * b;
-    rz += (double)r * (double)z;
     rr += (double)r * (double)r;
   }
   block_add(bb, c.acc + A_BB);
-  block_add(rz, c.acc + A_RZ0);
   block_add(rr, c.acc + A_RR0);
   if (!grid_sync(c)) return;
   bb = *(volatile double*)(c.acc + A_BB);
-  rz = *(volatile double*)(c.acc + A_RZ0);
   rr = *(volatile double*)(c.acc + A_RR0);
   const double tol2 = c.rtol * c.rtol * bb;
-  int k = 0;
   bool conv = (bb == 0.0) || (rr <= tol2);
+  double gamma = 0, delta = 0, alpha = 0;
+  if (!conv) {
+    if (!precond(v, mg, c, M, c.acc + A_RU0)) return;
+    if (!grid_sync(c)) return;
+    gamma = *(volatile double*)(c.acc + A_RU0);
+    double du = 0;
+    for (int i = tid; i < M; i += nth) {
+      const T w = band_apply(v, v.u, i);
+      const T u = v.u[i];
+      v.p[i] = u;
+      v.q[i] = w;
+      du += (double)w * (double)u;
+    }
+    block_add(du, c.acc + A_DU0);
+    if (!grid_sync(c)) return;
+    delta = *(volatile double*)(c.acc + A_DU0);
+    if (!(delta > 0.0)) conv = true;
+    alpha = conv ? 0.0 : gamma / delta;
+  }
+  int k = 0;
   while (!conv && k < c.maxit) {
     const int par = k & 1;
-    double pq = 0;
+    const T a = (T)alpha;
+    double rrn = 0;
     for (int i = tid; i < M; i += nth) {
-      const long long p = idx[i];
-      const T q = neg_lap_apply(g, mc, v, v.p, p);
-      v.q[p] = q;
-      pq += (double)v.p[p] * (double)q;
-    }
-    block_add(pq, c.acc + A_PQ + par);
-    if (!grid_sync(c)) return;
-    pq = *(volatile double*)(c.acc + A_PQ + par);
-    if (!(pq > 0.0)) break;
-    const T alpha = (T)(rz / pq);
-    double rzn = 0, rrn = 0;
-    for (int i = tid; i < M; i += nth) {
-      const long long p = idx[i];
-      v.x[p] += alpha * v.p[p];
-      const T r = v.r[p] - alpha * v.q[p];
-      v.r[p] = r;
-      const T z = r * v.idg[p];
-      rzn += (double)r * (double)z;
+      v.x[i] += a * v.p[i];
+      const T r = v.r[i] - a * v.q[i];
+      v.r[i] = r;
       rrn += (double)r * (double)r;
     }
-    block_add(rzn, c.acc + A_RZ + par);
     block_add(rrn, c.acc + A_RR + par);
     if (!grid_sync(c)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_PQ + par] = 0.0;
-    rzn = *(volatile double*)(c.acc + A_RZ + par);
-    rrn = *(volatile double*)(c.acc + A_RR + par);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_DU + (par ^ 1)] = 0.0;
+    rr = *(volatile double*)(c.acc + A_RR + par);
     ++k;
-    rr = rrn;
-    if (rrn <= tol2) {
+    if (rr <= tol2) {
       conv = true;
       break;
     }
-    const T beta = (T)(rzn / rz);
-    rz = rzn;
-    for (int i = tid; i < M; i += nth) {
-      const long long p = idx[i];
-      v.p[p] = v.r[p] * v.idg[p] + beta * v.p[p];
-    }
+    if (!precond(v, mg, c, M, c.acc + A_RU + par)) return;
     if (!grid_sync(c)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      c.acc[A_RZ + par] = 0.0;
-      c.acc[A_RR + par] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_RR + par] = 0.0;
+    const double gnew = *(volatile double*)(c.acc + A_RU + par);
+    const double beta = gnew / gamma;
+    const T bt = (T)beta;
+    double dun = 0;
+    for (int i = tid; i < M; i += nth) {
+      const T w = band_apply(v, v.u, i);
+      const T u = v.u[i];
+      v.p[i] = u + bt * v.p[i];
+      v.q[i] = w + bt * v.q[i];
+      dun += (double)w * (double)u;
     }
+    block_add(dun, c.acc + A_DU + par);
+    if (!grid_sync(c)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_RU + par] = 0.0;
+    delta = *(volatile double*)(c.acc + A_DU + par);
+    const double den = delta - beta * gnew / alpha;
+    if (!(den > 0.0)) break;
+    alpha = gnew / den;
+    gamma = gnew;
   }
   // zero-mean projection of the solution (single band component)
   if (!grid_sync(c)) return;
   double sx = 0;
-  for (int i = tid; i < M; i += nth) sx += (double)v.x[idx[i]];
+  for (int i = tid; i < M; i += nth) sx += (double)v.x[i];
   block_add(sx, c.acc + A_SUMX);
   if (!grid_sync(c)) return;
   const T mx = (T)(*(volatile double*)(c.acc + A_SUMX) / M);
-  for (int i = tid; i < M; i += nth) v.x[idx[i]] -= mx;
+  for (int i = tid; i < M; i += nth) wfull[idx[i]] = v.x[i] - mx;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *c.iters = k;
     *c.resid = bb > 0 ? sqrt(rr / bb) : 0.0;
-    atomicAdd(c.work, (unsigned long long)(k + 3) * (unsigned long long)M);
     if (!conv) atomicCAS(c.status, 0, 5);
+    atomicAdd(c.work, (unsigned long long)(k + 3) * (unsigned long long)M);
   }
 }
 
@@ -679,7 +936,7 @@ __global__ void k_band_dot(const int* __restrict__ idx, const int* __restrict__ 
   const int M = *count;
   double s = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const long long p = idx[i];
+    const int p = idx[i];
     s += (double)w[p] * rhs(p);
   }
   block_add(s, dst);

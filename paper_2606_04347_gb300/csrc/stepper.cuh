@@ -247,6 +247,10 @@ template <typename T> class Stepper : public PlanBase {
     g_.ny = ny;
     g_.nz = nz;
     g_.nxh = nx / 2 + 1;
+    g_.lx = 0;
+    while ((1 << g_.lx) < nx) ++g_.lx;
+    g_.ly = 0;
+    while ((1 << g_.ly) < ny) ++g_.ly;
     g_.n = (long long)nx * ny * nz;
     g_.nhat = (long long)g_.nxh * ny * nz;
     g_.hx = 2.0 * P_.half_len[0] / nx;
@@ -307,10 +311,14 @@ template <typename T> class Stepper : public PlanBase {
     sS_ = alloc<C>(g_.nhat);
     sSu_ = alloc<C>(g_.nhat);
     T** reals[] = {&phiA_, &phiB_, &phit_, &lap_, &gx_, &gy_, &gz_, &lu_, &rr_, &wm_, &r2_, &ut_, &G_, &w_,
-                   &cg_.r, &cg_.p, &cg_.q, &cg_.cx, &cg_.cy, &cg_.cz, &cg_.idg};
+                   &cg_.x, &cg_.r, &cg_.u, &cg_.p, &cg_.q, &cg_.idg};
     for (T** r : reals) *r = alloc<T>(g_.n);
     for (T** r : reals) ETD_CUDA(cudaMemset(*r, 0, sizeof(T) * g_.n));
-    cg_.x = w_;
+    cg_.cap = (int)g_.n;
+    cg_.c = alloc<T>(6 * (size_t)g_.n);
+    cg_.nb = alloc<int>(6 * (size_t)g_.n);
+    bmap_ = alloc<int>(g_.n);
+    init_multigrid();
     mask_ = alloc<unsigned char>(g_.n);
     idx_ = alloc<int>(g_.n);
     idx_old_ = alloc<int>(g_.n);
@@ -504,21 +512,20 @@ template <typename T> class Stepper : public PlanBase {
     });
     timed(ETD_K_BAND, 8.0 * nblk_, [&] { k_band_scan<<<1, 1024, 0, st_>>>(nblk_, bcount_, count_); });
     timed(ETD_K_BAND, (double)g_.n, [&] {
-      k_band_scatter<<<nblk_, kCompactBlock, 0, st_>>>(g_.n, mask_, bcount_, idx_);
+      k_band_scatter<<<nblk_, kCompactBlock, 0, st_>>>(g_.n, mask_, bcount_, idx_, bmap_);
     });
     ETD_CUDA(cudaGetLastError());
   }
 
   void cg_setup(const T* G) {
     CGVec<T> v = cg_;
-    timed(ETD_K_BAND, 0.0, [&] { k_cg_setup<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, mask_, G, v); });
-    timed(ETD_K_BAND, 0.0, [&] { k_cg_diag<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, v); });
+    timed(ETD_K_BAND, 0.0, [&] { k_cg_setup<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, mask_, bmap_, G, v); });
+    mg_setup();
     ETD_CUDA(cudaGetLastError());
   }
 
   template <typename Rhs> void cg_solve(Rhs rhs, T* x) {
     CGVec<T> v = cg_;
-    v.x = x;
     CGCtl c;
     c.acc = acc_;
     c.bar = bar_;
@@ -533,15 +540,121 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaMemsetAsync(bar_, 0, sizeof(unsigned) * 2, st_));
     auto k = k_cg<T, Rhs>;
     int per = 0;
-    ETD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, 0));
+    ETD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 1024, 0));
     if (per < 1) throw Error(ETD_ECUDA, "band CG kernel cannot be resident");
-    const int grid = nsm_ * std::min(per, 4);
-    Geo g = g_;
-    ModelC<T> mc = mc_;
+    const int grid = nsm_;
     const int* idx = idx_;
     const int* cnt = count_;
-    void* args[] = {&g, &mc, &idx, &cnt, &v, &rhs, &c};
-    timed(ETD_K_CG, 0.0, [&] { ETD_CUDA(cudaLaunchCooperativeKernel((const void*)k, grid, 256, args, 0, st_)); });
+    T* wfull = x;
+    MGP<T> mg = mgp();
+    void* args[] = {&idx, &cnt, &v, &wfull, &rhs, &c, &mg};
+    timed(ETD_K_CG, 0.0, [&] { ETD_CUDA(cudaLaunchCooperativeKernel((const void*)k, grid, 1024, args, 0, st_)); });
+  }
+
+  // Level l coarsens the grid 2x per axis l times (z only in 3D) while every coarsened
+  // extent stays >= 4; levels whose full grid has >= 2^17 cells run on the whole GPU in the
+  // V-cycle, smaller ones on one block.
+  void init_multigrid() {
+    int lz = 0;
+    while ((1 << lz) < g_.nz) ++lz;
+    HostLevel& L0 = lv_[0];
+    L0.lx = g_.lx;
+    L0.ly = g_.ly;
+    L0.lz = lz;
+    L0.cap = (int)g_.n;
+    L0.agg = alloc<int>(g_.n);
+    L0.e = alloc<T>(g_.n);
+    ETD_CUDA(cudaMemset(L0.e, 0, sizeof(T) * g_.n));
+    mg_nlev_ = 1;
+    const bool is3d = g_.nz > 1;
+    while (mg_nlev_ < kMGMax) {
+      const HostLevel& F = lv_[mg_nlev_ - 1];
+      if (F.lx < 3 || F.ly < 3 || (is3d && F.lz < 3)) break;
+      HostLevel& L = lv_[mg_nlev_];
+      L.lx = F.lx - 1;
+      L.ly = F.ly - 1;
+      L.lz = is3d ? F.lz - 1 : 0;
+      L.cap = 1 << (L.lx + L.ly + L.lz);
+      L.nblk = (L.cap + kCompactBlock - 1) / kCompactBlock;
+      L.cnt = alloc<int>(1);
+      L.list = alloc<int>(L.cap);
+      L.map = alloc<int>(L.cap);
+      L.bcount = alloc<int>(L.nblk);
+      L.mark = alloc<unsigned char>(L.cap);
+      L.c = alloc<T>(6 * (size_t)L.cap);
+      L.nb = alloc<int>(6 * (size_t)L.cap);
+      L.idg = alloc<T>(L.cap);
+      L.agg = alloc<int>(L.cap);
+      L.child = alloc<int>(8 * (size_t)L.cap);
+      L.b = alloc<T>(L.cap);
+      L.e = alloc<T>(L.cap);
+      L.o = alloc<T>(L.cap);
+      ETD_CUDA(cudaMemset(L.cnt, 0, sizeof(int)));
+      ++mg_nlev_;
+    }
+    mg_gl_ = 1;
+    while (mg_gl_ < mg_nlev_ && lv_[mg_gl_].cap >= (1 << 17)) ++mg_gl_;
+  }
+
+  // Coarse levels for the current band (level 0 = idx_, count_, mask_, bmap_, cg_).
+  void mg_setup() {
+    const int is3d = g_.nz > 1;
+    for (int l = 1; l < mg_nlev_; ++l) {
+      HostLevel& L = lv_[l];
+      const HostLevel& F = lv_[l - 1];
+      const int* flist = l == 1 ? idx_ : F.list;
+      const int* fcnt = l == 1 ? count_ : F.cnt;
+      const unsigned char* fmark = l == 1 ? mask_ : F.mark;
+      const int* fmap = l == 1 ? bmap_ : F.map;
+      const T* fc = l == 1 ? cg_.c : F.c;
+      int* fagg = lv_[l - 1].agg;
+      timed(ETD_K_BAND, 0.0, [&] {
+        ETD_CUDA(cudaMemsetAsync(L.mark, 0, L.cap, st_));
+        k_mg_mark<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.lx, F.ly, is3d, L.lx, L.ly, L.mark);
+        k_mask_count<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount);
+        k_band_scan<<<1, 1024, 0, st_>>>(L.nblk, L.bcount, L.cnt);
+        k_band_scatter<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount, L.list, L.map);
+        k_mg_parent<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.lx, F.ly, is3d, L.lx, L.ly, L.map, fagg);
+        k_mg_coarse<T><<<nsm_ * 4, 256, 0, st_>>>(L.list, L.cnt, L.lx, L.ly, L.lz, is3d, fmark, fmap, F.lx, F.ly, fc,
+                                                  F.cap, L.map, L.c, L.nb, L.idg, L.child, L.cap);
+      });
+      ETD_CUDA(cudaGetLastError());
+    }
+  }
+
+  MGP<T> mgp() const {
+    MGP<T> m{};
+    m.nlev = mg_nlev_;
+    m.gl = mg_gl_;
+    m.csweeps = 2;
+    m.omega = (T)(2.0 / 3.0);
+    for (int l = 0; l < mg_nlev_; ++l) {
+      const HostLevel& H = lv_[l];
+      MGL<T>& L = m.L[l];
+      L.cap = H.cap;
+      L.agg = H.agg;
+      L.e = H.e;
+      if (l == 0) {
+        L.cnt = count_;
+        L.list = idx_;
+        L.c = cg_.c;
+        L.nb = cg_.nb;
+        L.idg = cg_.idg;
+        L.child = nullptr;
+        L.b = cg_.r;
+        L.o = cg_.u;
+      } else {
+        L.cnt = H.cnt;
+        L.list = H.list;
+        L.c = H.c;
+        L.nb = H.nb;
+        L.idg = H.idg;
+        L.child = H.child;
+        L.b = H.b;
+        L.o = H.o;
+      }
+    }
+    return m;
   }
 
   void set_a0_if_needed() {
@@ -786,6 +899,17 @@ template <typename T> class Stepper : public PlanBase {
     *w_ = nullptr;
   CGVec<T> cg_{};
   unsigned char* mask_ = nullptr;
+  int* bmap_ = nullptr;
+  // multigrid hierarchy of the band solve (level 0 = the band itself)
+  struct HostLevel {
+    int lx = 0, ly = 0, lz = 0, cap = 0, nblk = 0;
+    int *cnt = nullptr, *list = nullptr, *map = nullptr, *bcount = nullptr;
+    unsigned char* mark = nullptr;
+    T *c = nullptr, *idg = nullptr, *b = nullptr, *e = nullptr, *o = nullptr;
+    int *nb = nullptr, *agg = nullptr, *child = nullptr;
+  };
+  HostLevel lv_[kMGMax];
+  int mg_nlev_ = 1, mg_gl_ = 1;
   int *idx_ = nullptr, *idx_old_ = nullptr, *bcount_ = nullptr, *count_ = nullptr, *count_old_ = nullptr;
   int nblk_ = 0;
   T* tab_ = nullptr;
