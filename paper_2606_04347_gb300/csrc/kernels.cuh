@@ -606,13 +606,16 @@ template <typename T> struct MGL {
   T* b;                // right-hand side (level 0: the CG residual r)
   T* e;                // pre-smoothed correction
   T* o;                // output correction (level 0: the preconditioned residual u)
+  T* t;                // scratch: residual handed to the restriction, first post-sweep
 };
 
 template <typename T> struct MGP {
   int nlev;            // 1 = plain Jacobi
   int gl;              // levels 0..gl-1 are processed by the whole grid, the rest by block 0
   int csweeps;         // Jacobi sweeps on the coarsest level (even)
+  int nu;              // pre- and post-smoothing sweeps (1 or 2)
   T omega;
+  T alpha;             // over-correction of the coarse-grid correction
   MGL<T> L[kMGMax];
 };
 
@@ -703,21 +706,24 @@ struct PhaseSync {
   }
 };
 
-// u = V(r), one symmetric V(1,1) cycle.  On entry r (level-0 b) is complete and visible;
-// on return every block has written its share of u (level-0 o) and added its part of (r,u)
-// to *ru.  Returns false when a barrier failed.
+// u = V(r), one symmetric V(nu,nu) cycle (nu = 1 or 2 weighted-Jacobi sweeps before and
+// after the coarse-grid correction, which is scaled by alpha).  On entry r (level-0 b) is
+// complete and visible; on return every block has written its share of u (level-0 o) and
+// added its part of (r,u) to *ru.  Residuals of the pre-sweeps are carried algebraically:
+// e1 = w D^-1 b, r1 = b - A e1 (needs b at the neighbours), e2 = e1 + w D^-1 r1,
+// r2 = r1 - w A D^-1 r1 (needs r1 at the neighbours).  Returns false if a barrier failed.
 template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c, double* ru) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   PhaseSync ps{true, true};
-  const T om = mg.omega;
+  const T om = mg.omega, al = mg.alpha;
   for (int l = 0; l < mg.nlev - 1; ++l) {
     const MGL<T>& L = mg.L[l];
     bool grid = l < mg.gl;
+    int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
     if (!ps.step(grid, c)) return false;
-    // pre-smoothing from zero, e = omega D^{-1} b, and the residual b - A e, which needs
-    // only b at the neighbours (complete before this phase); the residual is parked in o
     if (grid || blockIdx.x == 0) {
-      const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x, M = *L.cnt;
+      T* r1out = mg.nu == 2 ? L.o : L.t;
+      const int M = *L.cnt;
       for (int i = t0; i < M; i += ns) {
         const T ei = om * L.idg[i] * L.b[i];
         T s = 0;
@@ -727,21 +733,39 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
           s += L.c[f * L.cap + i] * (ei - om * L.idg[j] * L.b[j]);
         }
         L.e[i] = ei;
-        L.o[i] = L.b[i] - s;
+        r1out[i] = L.b[i] - s;
       }
     }
-    // restriction: sum of the children's residuals
+    if (mg.nu == 2) {
+      if (!ps.step(grid, c)) return false;
+      if (grid || blockIdx.x == 0) {
+        const int M = *L.cnt;
+        for (int i = t0; i < M; i += ns) {
+          const T di = L.idg[i] * L.o[i];
+          T s = 0;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            const int j = L.nb[f * L.cap + i];
+            s += L.c[f * L.cap + i] * (di - L.idg[j] * L.o[j]);
+          }
+          L.e[i] += om * di;
+          L.t[i] = L.o[i] - om * s;
+        }
+      }
+    }
     const MGL<T>& Cl = mg.L[l + 1];
     grid = (l + 1) < mg.gl;
+    t0 = grid ? tid : threadIdx.x;
+    ns = grid ? nth : blockDim.x;
     if (!ps.step(grid, c)) return false;
     if (grid || blockIdx.x == 0) {
-      const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x, M = *Cl.cnt;
+      const int M = *Cl.cnt;
       for (int I = t0; I < M; I += ns) {
         T s = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = Cl.child[q * Cl.cap + I];
-          if (j >= 0) s += L.o[j];
+          if (j >= 0) s += L.t[j];
         }
         Cl.b[I] = s;
       }
@@ -770,21 +794,34 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     const MGL<T>& L = mg.L[l];
     const MGL<T>& Cl = mg.L[l + 1];
     const bool grid = l < mg.gl;
+    const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
     if (!ps.step(grid, c)) return false;
     double acc = 0;
     if (grid || blockIdx.x == 0) {
-      const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x, M = *L.cnt;
+      T* out = mg.nu == 2 ? L.t : L.o;
+      const int M = *L.cnt;
       for (int i = t0; i < M; i += ns) {
-        const T ei = L.e[i] + Cl.o[L.agg[i]];
+        const T ei = L.e[i] + al * Cl.o[L.agg[i]];
         T s = 0;
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           const int j = L.nb[f * L.cap + i];
-          s += L.c[f * L.cap + i] * (ei - (L.e[j] + Cl.o[L.agg[j]]));
+          s += L.c[f * L.cap + i] * (ei - (L.e[j] + al * Cl.o[L.agg[j]]));
         }
-        const T out = ei + om * L.idg[i] * (L.b[i] - s);
-        L.o[i] = out;
-        if (l == 0) acc += (double)L.b[i] * (double)out;
+        const T o1 = ei + om * L.idg[i] * (L.b[i] - s);
+        out[i] = o1;
+        if (l == 0 && mg.nu == 1) acc += (double)L.b[i] * (double)o1;
+      }
+    }
+    if (mg.nu == 2) {
+      if (!ps.step(grid, c)) return false;
+      if (grid || blockIdx.x == 0) {
+        const int M = *L.cnt;
+        for (int i = t0; i < M; i += ns) {
+          const T o2 = L.t[i] + om * L.idg[i] * (L.b[i] - mg_apply(L, L.t, i));
+          L.o[i] = o2;
+          if (l == 0) acc += (double)L.b[i] * (double)o2;
+        }
       }
     }
     if (l == 0) block_add(acc, ru);

@@ -552,8 +552,10 @@ template <typename T> class Stepper : public PlanBase {
   }
 
   // Level l coarsens the grid 2x per axis l times (z only in 3D) while every coarsened
-  // extent stays >= 4; levels whose full grid has >= 2^17 cells run on the whole GPU in the
-  // V-cycle, smaller ones on one block.
+  // extent stays >= 4; levels whose full grid has >= 2^15 cells run on the whole GPU in the
+  // V-cycle, smaller ones on one block.  The cycle is V(2,2) with Jacobi (omega = 2/3), the
+  // coarse-grid correction over-corrected by 1.9 (piecewise-constant aggregation
+  // under-estimates it) and 2 Jacobi sweeps on the coarsest level.
   void init_multigrid() {
     int lz = 0;
     while ((1 << lz) < g_.nz) ++lz;
@@ -564,7 +566,9 @@ template <typename T> class Stepper : public PlanBase {
     L0.cap = (int)g_.n;
     L0.agg = alloc<int>(g_.n);
     L0.e = alloc<T>(g_.n);
+    L0.t = alloc<T>(g_.n);
     ETD_CUDA(cudaMemset(L0.e, 0, sizeof(T) * g_.n));
+    ETD_CUDA(cudaMemset(L0.t, 0, sizeof(T) * g_.n));
     mg_nlev_ = 1;
     const bool is3d = g_.nz > 1;
     while (mg_nlev_ < kMGMax) {
@@ -589,11 +593,12 @@ template <typename T> class Stepper : public PlanBase {
       L.b = alloc<T>(L.cap);
       L.e = alloc<T>(L.cap);
       L.o = alloc<T>(L.cap);
+      L.t = alloc<T>(L.cap);
       ETD_CUDA(cudaMemset(L.cnt, 0, sizeof(int)));
       ++mg_nlev_;
     }
     mg_gl_ = 1;
-    while (mg_gl_ < mg_nlev_ && lv_[mg_gl_].cap >= (1 << 17)) ++mg_gl_;
+    while (mg_gl_ < mg_nlev_ && lv_[mg_gl_].cap >= (1 << 15)) ++mg_gl_;
   }
 
   // Coarse levels for the current band (level 0 = idx_, count_, mask_, bmap_, cg_).
@@ -627,13 +632,16 @@ template <typename T> class Stepper : public PlanBase {
     m.nlev = mg_nlev_;
     m.gl = mg_gl_;
     m.csweeps = 2;
+    m.nu = 2;
     m.omega = (T)(2.0 / 3.0);
+    m.alpha = (T)1.9;
     for (int l = 0; l < mg_nlev_; ++l) {
       const HostLevel& H = lv_[l];
       MGL<T>& L = m.L[l];
       L.cap = H.cap;
       L.agg = H.agg;
       L.e = H.e;
+      L.t = H.t;
       if (l == 0) {
         L.cnt = count_;
         L.list = idx_;
@@ -905,7 +913,7 @@ template <typename T> class Stepper : public PlanBase {
     int lx = 0, ly = 0, lz = 0, cap = 0, nblk = 0;
     int *cnt = nullptr, *list = nullptr, *map = nullptr, *bcount = nullptr;
     unsigned char* mark = nullptr;
-    T *c = nullptr, *idg = nullptr, *b = nullptr, *e = nullptr, *o = nullptr;
+    T *c = nullptr, *idg = nullptr, *b = nullptr, *e = nullptr, *o = nullptr, *t = nullptr;
     int *nb = nullptr, *agg = nullptr, *child = nullptr;
   };
   HostLevel lv_[kMGMax];
