@@ -87,30 +87,13 @@ etd_status run(int dim, const int* n, const void* field, void* half, cudaStream_
   g.n = (long long)nx * ny * nz;
   g.nhat = (long long)g.nxh * ny * nz;
   const size_t inter = align256(sizeof(C) * (size_t)g.nhat);
-  // same tile rule as a plan: ZB planes per pass-A CTA, largest Y2 whose buffers fit
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t budget = std::min<size_t>((size_t)optin, 200 * 1024);
-  const size_t cs = sizeof(C);
-  g.ZB = nz == 1 ? 1 : std::min(nz, cs == 8 ? 4 : 2);
-  g.Y2 = 0;
-  for (int y2 = ny; y2 >= 2; y2 >>= 1) {
-    const int y1 = ny / y2;
-    if (2 * (size_t)g.ZB * y2 * g.nxh * cs <= budget && 3 * (size_t)y1 * nz * cs <= budget) {
-      g.Y2 = y2;
-      break;
-    }
-  }
-  if (!g.Y2) {
-    etd::set_last_error("grid too large for the two-pass FFT tiles");
+  // same tile rule as a plan
+  size_t smemA = 0, smemB1 = 0;
+  if (!etd::choose_tiles(g, sizeof(C), smemA, smemB1)) {
+    etd::set_last_error("grid not supported by the two-pass FFT tiles");
     return ETD_EINVAL;
   }
-  g.Y1 = ny / g.Y2;
-  const size_t slot1 = (size_t)g.Y1 * nz * cs;
-  g.KB = nz > 1 ? 1 : (int)std::max<size_t>(1, std::min<size_t>((size_t)g.nxh, (48 * 1024) / (3 * slot1)));
-  const size_t smemA = 2 * (size_t)g.ZB * g.Y2 * g.nxh * cs;
-  const size_t smemB = 3 * (size_t)g.KB * g.Y1 * nz * cs;
+  const size_t smemB = smemB1;  // one operand tile (forward only)
 
   C* I = reinterpret_cast<C*>(scratch);
   C* twx = reinterpret_cast<C*>(scratch + inter);
@@ -124,7 +107,7 @@ etd_status run(int dim, const int* n, const void* field, void* half, cudaStream_
   auto kb = etd::passB<T, etd::OpToStd<T>>;
   if (smemA > 48 * 1024) cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
   if (smemB > 48 * 1024) cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
-  ka<<<(nz / g.ZB) * g.Y1, 512, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy);
+  ka<<<(nz / g.ZB) * g.Y1, 256, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy);
   etd::OpToStd<T> op{0, static_cast<C*>(half), g.ny, g.nxh};
   etd::OutP<C> outs{};
   const int nkb = (g.nxh + g.KB - 1) / g.KB;

@@ -3,22 +3,26 @@
 // Transform convention (the spectral collocation of Sec. 3.2): forward
 //   F_k = sum_j f_j exp(-2 pi i j.k / N), inverse with +i and 1/N.
 //
-// Decomposition ("four-step" split of the y axis, Ny = Y1 * Y2, y = n1 + Y1 * n2,
-// ky = k2 + Y2 * k1):
+// Decomposition ("four-step" split of the y axis, Ny = Y1 * Y2 with Y2 = min(Ny, 16),
+// y = n1 + Y1 * n2, ky = k2 + Y2 * k1):
 //   pass A (one CTA per z-block of ZB planes and residue n1): the Y2 rows y = n1 + Y1*j of
 //     each plane are real-to-complex transformed along x (two real rows packed into one
 //     complex row), then Y2-point DFTs across the rows give k2, then the twiddle
 //     w_Ny^(n1 k2).  Out: intermediate I[k2][kx][n1][z].
-//   pass B (one CTA per kx-block and k2): the Y1-point DFT over n1 gives k1, the Nz-point
-//     DFT over z gives kz.  The spectrum sits in smem; a pointwise spectral operator runs
-//     there (the ETD update), and the results go straight back through the inverse pass B.
+//   pass B (one CTA per kx and k2): the Y1-point DFT over n1 gives k1, the Nz-point DFT over
+//     z gives kz.  The spectrum sits in registers; a pointwise spectral operator runs there
+//     (the ETD update), and the results go straight back through the inverse pass B.
 // The spectral layout is therefore S[k2][kx][k1][kz] (complex), the same index map as the
 // intermediate, so stored spectra are read and written by pass B in contiguous chunks.
 //
-// In shared memory every 1D transform is a batched Stockham autosort FFT (radix 8/4/2,
-// ping-pong between two buffers, one barrier per stage), the formulation of Govindaraju et
-// al., "High performance discrete Fourier transforms on graphics processors" (SC 2008).
-// Twiddles come from per-axis FP64-built tables w_N^e = exp(-2 pi i e/N), e < N.
+// Long transforms (x in pass A, z in pass B) run on a team of S lanes of one warp holding
+// R = L/S values each: an R-point DFT in registers, a twiddle w_L^(t k1), and log2 S
+// radix-2 decimation-in-frequency stages across the lanes by warp shuffles, which leave
+// lane t holding X[k1 + R * bitrev(t)].  The inverse runs the conjugate-transposed stages
+// in reverse order, so it takes that bit-reversed layout and returns natural order (and
+// coalesced stores).  Short transforms across rows (Y1, Y2 <= 16) run one column per
+// thread in registers.  Shared memory holds one padded tile per operand; twiddles come
+// from per-axis tables w_N^e = exp(-2 pi i e/N) built in FP64.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,6 +51,32 @@ struct Geo {
   long long n, nhat;
   double hx, hy, hz;
 };
+
+// Shared-memory padding: one spare slot every 16 complex elements (bank spreading).
+__host__ __device__ __forceinline__ int pad16(int k) { return k + (k >> 4); }
+
+// Lanes per team for a transform of length L (R = L / S values per lane).
+__host__ __device__ __forceinline__ int team_lanes(int L) { return L >= 64 ? 32 : (L >= 2 ? L / 2 : 1); }
+
+// Tile choice shared by the plan and the allocation-free entry point.  Returns false if the
+// grid is not supported.  smemA: pass-A tile; smemB1: one pass-B operand tile.
+inline bool choose_tiles(Geo& g, size_t csize, size_t& smemA, size_t& smemB1) {
+  g.Y2 = g.ny < 16 ? g.ny : 16;
+  g.Y1 = g.ny / g.Y2;
+  if (g.Y1 > 16 || g.Y2 < 2) return false;
+  g.ZB = g.nz == 1 ? 1 : (g.nz < (csize == 8 ? 4 : 2) ? g.nz : (csize == 8 ? 4 : 2));
+  const int rsa = pad16(g.nxh - 1) + 1;
+  smemA = (size_t)g.ZB * g.Y2 * rsa * csize;
+  if (g.nz > 1) {
+    g.KB = 1;
+  } else {
+    g.KB = 512 / g.Y1;
+    if (g.KB > g.nxh) g.KB = g.nxh;
+  }
+  const int rsb = pad16(g.nz - 1) + 1;
+  smemB1 = (size_t)g.KB * g.Y1 * rsb * csize;
+  return smemA <= 200 * 1024 && 2 * smemB1 <= 200 * 1024;
+}
 
 // ---- radix kernels --------------------------------------------------------------------
 template <typename C, bool INV> __device__ __forceinline__ void dft2(C* v) {
@@ -99,69 +129,80 @@ template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C* v
   else dft8<C, INV>(v);
 }
 
-// One Stockham stage: `nbatch` transforms of length L, current span Ns.  Element i of
-// transform b lives at base(b) + i*es, base(b) = (b / nb_in) * bs_out + (b % nb_in) * bs_in.
-// batch_fast chooses which index varies fastest across threads (bank-conflict control).
-template <typename C, int R, bool INV>
-__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int L,
-                                               int Ns, int nbatch, int nb_in, int bs_in, int bs_out,
-                                               int es, const C* __restrict__ tw, int twstride,
-                                               bool batch_fast) {
-  const int nbf = L / R;
-  const int total = nbatch * nbf;
-  const int tstep = (L / (Ns * R)) * twstride;
-  for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    int b, j;
-    if (batch_fast) {
-      b = w % nbatch;
-      j = w / nbatch;
-    } else {
-      j = w % nbf;
-      b = w / nbf;
-    }
-    const int base = (b / nb_in) * bs_out + (b % nb_in) * bs_in;
-    C v[R];
+
+// 16-point DFT as 4 x 4 (inner DFT4 over n2 for each n1, twiddle w16^(n1 k1), outer DFT4).
+template <typename C, bool INV> __device__ __forceinline__ void dft16(C* v) {
+  using T = decltype(v[0].x);
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, h = (T)0.70710678118654752440;
+  const C w[10] = {C{1, 0}, C{c1, -s1}, C{h, -h}, C{s1, -c1}, C{0, -1}, C{-s1, -c1}, C{-h, -h}, C{-c1, -s1},
+                   C{-1, 0}, C{-c1, s1}};
+  C a[4][4];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[base + (j + r * nbf) * es];
-    const int k = j & (Ns - 1);
-    if (Ns > 1) {
+  for (int n1 = 0; n1 < 4; ++n1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C t = __ldg(&tw[r * k * tstep]);
-        v[r] = INV ? cmulc(v[r], t) : cmul(v[r], t);
-      }
-    }
-    dftR<C, R, INV>(v);
-    const int ob = (j - k) * R + k;
+    for (int n2 = 0; n2 < 4; ++n2) a[n1][n2] = v[n1 + 4 * n2];
+    dft4<C, INV>(a[n1]);
+  }
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[base + (ob + r * Ns) * es] = v[r];
+  for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) a[n1][k1] = INV ? cmulc(a[n1][k1], w[n1 * k1]) : cmul(a[n1][k1], w[n1 * k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<C, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
   }
 }
 
-// Batched in-smem FFT of length L (a power of two); returns the buffer holding the result
-// (a or b).  Contains __syncthreads(): every thread of the block must call it.
-template <typename C, bool INV>
-__device__ C* smem_fft(C* a, C* b, int L, int nbatch, int nb_in, int bs_in, int bs_out, int es,
-                       const C* __restrict__ tw, int twstride, bool batch_fast) {
-  C* src = a;
-  C* dst = b;
-  int Ns = 1;
-  while (Ns < L) {
-    const int rem = L / Ns;
-    const int R = (rem == 16) ? 4 : (rem >= 8 ? 8 : rem);
-    if (R == 8)
-      stockham_stage<C, 8, INV>(src, dst, L, Ns, nbatch, nb_in, bs_in, bs_out, es, tw, twstride, batch_fast);
-    else if (R == 4)
-      stockham_stage<C, 4, INV>(src, dst, L, Ns, nbatch, nb_in, bs_in, bs_out, es, tw, twstride, batch_fast);
-    else
-      stockham_stage<C, 2, INV>(src, dst, L, Ns, nbatch, nb_in, bs_in, bs_out, es, tw, twstride, batch_fast);
-    __syncthreads();
-    C* t = src;
-    src = dst;
-    dst = t;
-    Ns *= R;
+// Natural-order DFT of compile-time length N in registers (N = 1, 2, 4, 8, 16).
+template <typename C, int N, bool INV> __device__ __forceinline__ void dftN(C* v) {
+  if (N == 2) dft2<C, INV>(v);
+  else if (N == 4) dft4<C, INV>(v);
+  else if (N == 8) dft8<C, INV>(v);
+  else if (N == 16) dft16<C, INV>(v);
+}
+
+template <typename C> __device__ __forceinline__ C shfl_xor_c(C v, int m) {
+  return C{__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
+}
+
+__device__ __forceinline__ int bitrev_bits(int t, int bits) { return bits ? (int)(__brev((unsigned)t) >> (32 - bits)) : 0; }
+
+// Team FFT of length L = R * S (S lanes, lane rank t; axes up to 256 points use R <= 8).  Forward: v[j] = x[t + S j] in,
+// v[k1] = X[k1 + R bitrev(t)] out.  Inverse: the reverse layouts, unnormalised.  Every
+// lane of the warp must call it (shuffles use the full mask).
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void team_fft(C (&v)[R], int t, int S, const C* __restrict__ tw) {
+  const int L = R * S;
+  if (!INV) {
+    dftN<C, R, false>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[t * k1]));
+    for (int h = S >> 1; h >= 1; h >>= 1) {
+      const C w = __ldg(&tw[(t & (h - 1)) * (L / (2 * h))]);
+      const bool up = (t & h) != 0;
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const C p = shfl_xor_c(v[k1], h);
+        v[k1] = up ? cmul(csub(p, v[k1]), w) : cadd(v[k1], p);
+      }
+    }
+  } else {
+    for (int h = 1; h < S; h <<= 1) {
+      const C w = __ldg(&tw[(t & (h - 1)) * (L / (2 * h))]);
+      const bool up = (t & h) != 0;
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const C p = shfl_xor_c(v[k1], h);
+        v[k1] = up ? csub(p, cmulc(v[k1], w)) : cadd(v[k1], cmulc(p, w));
+      }
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmulc(v[k1], __ldg(&tw[t * k1]));
+    dftN<C, R, true>(v);
   }
-  return src;
 }
 
 // Wavenumber bookkeeping of one spectral element.
@@ -190,190 +231,349 @@ __device__ __forceinline__ Wave make_wave(const Geo& g, int kx, int ky, int kz) 
   return w;
 }
 
-// ---- pass A: x real-to-complex + inner y DFT ------------------------------------------
-// smem: two buffers of ZB*Y2*nxh complex.
-template <typename T, typename Pro>
-__global__ void __launch_bounds__(512) passA_fwd(Geo g, Pro pro, typename Cplx<T>::type* __restrict__ out,
-                                                 const typename Cplx<T>::type* __restrict__ twx,
-                                                 const typename Cplx<T>::type* __restrict__ twy) {
-  using C = typename Cplx<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nrows = g.ZB * g.Y2;
-  const int tc = nrows * g.nxh;
-  C* bufA = reinterpret_cast<C*>(smem_raw);
-  C* bufB = bufA + tc;
-  const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
-  const int z0 = zb * g.ZB;
-  const int npairs = nrows >> 1;
-  for (int e = threadIdx.x; e < npairs * g.nx; e += blockDim.x) {
-    const int q = e / g.nx, x = e - q * g.nx;
-    const int r0 = 2 * q, r1 = r0 + 1;
-    const long long i0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx + x;
-    const long long i1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx + x;
-    bufA[e] = C{pro(i0), pro(i1)};
-  }
-  __syncthreads();
-  C* res = smem_fft<C, false>(bufA, bufB, g.nx, npairs, npairs, g.nx, 0, 1, twx, 1, false);
-  C* oth = (res == bufA) ? bufB : bufA;
-  const int mask = g.nx - 1;
-  for (int e = threadIdx.x; e < npairs * g.nxh; e += blockDim.x) {
-    const int q = e / g.nxh, k = e - q * g.nxh;
-    const C a = res[q * g.nx + k];
-    const C b = res[q * g.nx + ((g.nx - k) & mask)];
-    oth[(2 * q) * g.nxh + k] = C{(T)0.5 * (a.x + b.x), (T)0.5 * (a.y - b.y)};
-    oth[(2 * q + 1) * g.nxh + k] = C{(T)0.5 * (a.y + b.y), (T)0.5 * (b.x - a.x)};
-  }
-  __syncthreads();
-  C* r2 = smem_fft<C, false>(oth, res, g.Y2, g.ZB * g.nxh, g.nxh, 1, g.Y2 * g.nxh, g.nxh, twy, g.Y1, true);
-  for (int e = threadIdx.x; e < tc; e += blockDim.x) {
-    const int zz = e % g.ZB;
-    const int t = e / g.ZB;
-    const int kx = t % g.nxh, k2 = t / g.nxh;
-    C v = r2[(zz * g.Y2 + k2) * g.nxh + kx];
-    if (n1) v = cmul(v, __ldg(&twy[n1 * k2]));
-    out[((long long)(k2 * g.nxh + kx) * g.Y1 + n1) * g.nz + z0 + zz] = v;
-  }
-}
-
-template <typename T, typename Epi>
-__global__ void __launch_bounds__(512) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,
-                                                 const typename Cplx<T>::type* __restrict__ twx,
-                                                 const typename Cplx<T>::type* __restrict__ twy) {
-  using C = typename Cplx<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nrows = g.ZB * g.Y2;
-  const int tc = nrows * g.nxh;
-  C* bufA = reinterpret_cast<C*>(smem_raw);
-  C* bufB = bufA + tc;
-  const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
-  const int z0 = zb * g.ZB;
-  for (int e = threadIdx.x; e < tc; e += blockDim.x) {
-    const int zz = e % g.ZB;
-    const int t = e / g.ZB;
-    const int kx = t % g.nxh, k2 = t / g.nxh;
-    C v = in[((long long)(k2 * g.nxh + kx) * g.Y1 + n1) * g.nz + z0 + zz];
-    if (n1) v = cmulc(v, __ldg(&twy[n1 * k2]));
-    bufA[(zz * g.Y2 + k2) * g.nxh + kx] = v;
-  }
-  __syncthreads();
-  C* res = smem_fft<C, true>(bufA, bufB, g.Y2, g.ZB * g.nxh, g.nxh, 1, g.Y2 * g.nxh, g.nxh, twy, g.Y1, true);
-  C* oth = (res == bufA) ? bufB : bufA;
-  const int npairs = nrows >> 1;
-  const int h = g.nx >> 1;
-  for (int e = threadIdx.x; e < npairs * g.nx; e += blockDim.x) {
-    const int q = e / g.nx, k = e - q * g.nx;
-    C A, B;
-    if (k <= h) {
-      A = res[(2 * q) * g.nxh + k];
-      B = res[(2 * q + 1) * g.nxh + k];
-      if (k == 0 || k == h) {
-        A.y = 0;
-        B.y = 0;
-      }
-    } else {
-      A = res[(2 * q) * g.nxh + g.nx - k];
-      B = res[(2 * q + 1) * g.nxh + g.nx - k];
-      A.y = -A.y;
-      B.y = -B.y;
-    }
-    oth[e] = C{A.x - B.y, A.y + B.x};
-  }
-  __syncthreads();
-  C* r2 = smem_fft<C, true>(oth, res, g.nx, npairs, npairs, g.nx, 0, 1, twx, 1, false);
-  for (int e = threadIdx.x; e < npairs * g.nx; e += blockDim.x) {
-    const int q = e / g.nx, x = e - q * g.nx;
-    const int r0 = 2 * q, r1 = r0 + 1;
-    const long long i0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx + x;
-    const long long i1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx + x;
-    const C v = r2[e];
-    epi(i0, v.x);
-    epi(i1, v.y);
-  }
-}
 
 // Up to five output arrays of a pass-B launch, passed by value.
 template <typename C> struct OutP {
   C* p[5];
 };
 
-// ---- pass B: outer y DFT + z FFT, spectral operator, inverse ---------------------------
-// smem: three buffers of KB*Y1*nz complex.  Op supplies NI (intermediates to transform
-// forward, 0..2), combine(e, global index, wave, s0, s1) run elementwise on the spectra
-// (base result left in s0), nout outputs out(o, base, wave) inverse-transformed to outs[o].
-template <typename C>
-__device__ __forceinline__ C* passB_forward(const Geo& g, C* a, C* b, int kbn, const C* twy, const C* twz) {
-  C* r = smem_fft<C, false>(a, b, g.Y1, kbn * g.nz, g.nz, 1, g.Y1 * g.nz, g.nz, twy, g.Y2, true);
-  C* o = (r == a) ? b : a;
-  return smem_fft<C, false>(r, o, g.nz, kbn * g.Y1, kbn * g.Y1, g.nz, 0, 1, twz, 1, false);
+// ---- pass A: x real-to-complex + inner y DFT ------------------------------------------
+// Tile: rows r = zz * Y2 + j (plane z0 + zz, y = n1 + Y1 j), row stride pad16(nxh-1)+1.
+
+template <typename T, typename Pro, int R>
+__device__ __forceinline__ void passA_rows_fwd(const Geo& g, const Pro& pro, typename Cplx<T>::type* tile, int rs,
+                                               int z0, int n1, const typename Cplx<T>::type* __restrict__ twx) {
+  using C = typename Cplx<T>::type;
+  const int S = g.nx / R, lS = __ffs(S) - 1;
+  const int lane = threadIdx.x & 31, t = lane & (S - 1);
+  const int team = threadIdx.x / S, nteams = blockDim.x / S;
+  const int ncrows = (g.ZB * g.Y2) >> 1;
+  const int N = g.nx, half = g.nx >> 1;
+  constexpr int MU = R / 2 + 1;
+  for (int base = 0; base < ncrows; base += nteams) {
+    const int q = base + team;
+    const bool ok = q < ncrows;
+    C v[R];
+    const int r0 = 2 * q, r1 = r0 + 1;
+    const long long i0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx;
+    const long long i1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int x = t + S * j;
+      v[j] = ok ? C{pro(i0 + x), pro(i1 + x)} : C{0, 0};
+    }
+    team_fft<C, R, false>(v, t, S, twx);
+    C* row = tile + r0 * rs;
+    if (ok) {
+      const int br = bitrev_bits(t, lS);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) row[pad16(k1 + R * br)] = v[k1];
+    }
+    __syncwarp();
+    // unpack the two real rows: A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i)
+    C a[MU], b[MU];
+#pragma unroll
+    for (int m = 0; m < MU; ++m) {
+      const int k = t + S * m;
+      if (ok && k <= half) {
+        a[m] = row[pad16(k)];
+        b[m] = row[pad16((N - k) & (N - 1))];
+      }
+    }
+    __syncwarp();
+    if (ok) {
+#pragma unroll
+      for (int m = 0; m < MU; ++m) {
+        const int k = t + S * m;
+        if (k <= half) {
+          row[pad16(k)] = C{(T)0.5 * (a[m].x + b[m].x), (T)0.5 * (a[m].y - b[m].y)};
+          row[rs + pad16(k)] = C{(T)0.5 * (a[m].y + b[m].y), (T)0.5 * (b[m].x - a[m].x)};
+        }
+      }
+    }
+    __syncwarp();
+  }
 }
 
-template <typename C>
-__device__ __forceinline__ C* passB_inverse(const Geo& g, C* a, C* b, int kbn, const C* twy, const C* twz) {
-  C* r = smem_fft<C, true>(a, b, g.nz, kbn * g.Y1, kbn * g.Y1, g.nz, 0, 1, twz, 1, false);
-  C* o = (r == a) ? b : a;
-  return smem_fft<C, true>(r, o, g.Y1, kbn * g.nz, g.nz, 1, g.Y1 * g.nz, g.nz, twy, g.Y2, true);
+template <typename T, int Y>
+__device__ __forceinline__ void passA_cols_fwd(const Geo& g, const typename Cplx<T>::type* tile, int rs, int z0,
+                                               int n1, typename Cplx<T>::type* __restrict__ out,
+                                               const typename Cplx<T>::type* __restrict__ twy) {
+  using C = typename Cplx<T>::type;
+  const int ncols = g.ZB * g.nxh;
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    const int zz = col % g.ZB, kx = col / g.ZB;
+    C v[Y > 1 ? Y : 1];
+#pragma unroll
+    for (int j = 0; j < Y; ++j) v[j] = tile[(zz * Y + j) * rs + pad16(kx)];
+    dftN<C, Y, false>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < Y; ++k2) {
+      C x = v[k2];
+      if (n1) x = cmul(x, __ldg(&twy[n1 * k2]));
+      out[((long long)(k2 * g.nxh + kx) * g.Y1 + n1) * g.nz + z0 + zz] = x;
+    }
+  }
+}
+
+template <typename T, typename Pro>
+__global__ void __launch_bounds__(256) passA_fwd(Geo g, Pro pro, typename Cplx<T>::type* __restrict__ out,
+                                                 const typename Cplx<T>::type* __restrict__ twx,
+                                                 const typename Cplx<T>::type* __restrict__ twy) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tile = reinterpret_cast<C*>(smem_raw);
+  const int rs = pad16(g.nxh - 1) + 1;
+  const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
+  const int z0 = zb * g.ZB;
+  switch (g.nx / team_lanes(g.nx)) {
+    case 2: passA_rows_fwd<T, Pro, 2>(g, pro, tile, rs, z0, n1, twx); break;
+    case 4: passA_rows_fwd<T, Pro, 4>(g, pro, tile, rs, z0, n1, twx); break;
+    default: passA_rows_fwd<T, Pro, 8>(g, pro, tile, rs, z0, n1, twx); break;
+  }
+  __syncthreads();
+  switch (g.Y2) {
+    case 2: passA_cols_fwd<T, 2>(g, tile, rs, z0, n1, out, twy); break;
+    case 4: passA_cols_fwd<T, 4>(g, tile, rs, z0, n1, out, twy); break;
+    case 8: passA_cols_fwd<T, 8>(g, tile, rs, z0, n1, out, twy); break;
+    default: passA_cols_fwd<T, 16>(g, tile, rs, z0, n1, out, twy); break;
+  }
+}
+
+template <typename T, int Y>
+__device__ __forceinline__ void passA_cols_inv(const Geo& g, typename Cplx<T>::type* tile, int rs, int z0, int n1,
+                                               const typename Cplx<T>::type* __restrict__ in,
+                                               const typename Cplx<T>::type* __restrict__ twy) {
+  using C = typename Cplx<T>::type;
+  const int ncols = g.ZB * g.nxh;
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    const int zz = col % g.ZB, kx = col / g.ZB;
+    C v[Y > 1 ? Y : 1];
+#pragma unroll
+    for (int k2 = 0; k2 < Y; ++k2) {
+      C x = in[((long long)(k2 * g.nxh + kx) * g.Y1 + n1) * g.nz + z0 + zz];
+      if (n1) x = cmulc(x, __ldg(&twy[n1 * k2]));
+      v[k2] = x;
+    }
+    dftN<C, Y, true>(v);
+#pragma unroll
+    for (int j = 0; j < Y; ++j) tile[(zz * Y + j) * rs + pad16(kx)] = v[j];
+  }
+}
+
+template <typename T, typename Epi, int R>
+__device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, const typename Cplx<T>::type* tile,
+                                               int rs, int z0, int n1,
+                                               const typename Cplx<T>::type* __restrict__ twx) {
+  using C = typename Cplx<T>::type;
+  const int S = g.nx / R, lS = __ffs(S) - 1;
+  const int lane = threadIdx.x & 31, t = lane & (S - 1);
+  const int team = threadIdx.x / S, nteams = blockDim.x / S;
+  const int ncrows = (g.ZB * g.Y2) >> 1;
+  const int N = g.nx, half = g.nx >> 1;
+  const int br = bitrev_bits(t, lS);
+  for (int base = 0; base < ncrows; base += nteams) {
+    const int q = base + team;
+    const bool ok = q < ncrows;
+    const int r0 = 2 * q, r1 = r0 + 1;
+    const C* ra = tile + r0 * rs;
+    const C* rb = ra + rs;
+    C v[R];
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+      const int k = k1 + R * br;
+      C A = C{0, 0}, B = C{0, 0};
+      if (ok) {
+        if (k <= half) {
+          A = ra[pad16(k)];
+          B = rb[pad16(k)];
+          if (k == 0 || k == half) {
+            A.y = 0;
+            B.y = 0;
+          }
+        } else {
+          A = ra[pad16(N - k)];
+          B = rb[pad16(N - k)];
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+      }
+      v[k1] = C{A.x - B.y, A.y + B.x};
+    }
+    team_fft<C, R, true>(v, t, S, twx);
+    if (ok) {
+      const long long i0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx;
+      const long long i1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int x = t + S * j;
+        epi(i0 + x, v[j].x);
+        epi(i1 + x, v[j].y);
+      }
+    }
+  }
+}
+
+template <typename T, typename Epi>
+__global__ void __launch_bounds__(256) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,
+                                                 const typename Cplx<T>::type* __restrict__ twx,
+                                                 const typename Cplx<T>::type* __restrict__ twy) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tile = reinterpret_cast<C*>(smem_raw);
+  const int rs = pad16(g.nxh - 1) + 1;
+  const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
+  const int z0 = zb * g.ZB;
+  switch (g.Y2) {
+    case 2: passA_cols_inv<T, 2>(g, tile, rs, z0, n1, in, twy); break;
+    case 4: passA_cols_inv<T, 4>(g, tile, rs, z0, n1, in, twy); break;
+    case 8: passA_cols_inv<T, 8>(g, tile, rs, z0, n1, in, twy); break;
+    default: passA_cols_inv<T, 16>(g, tile, rs, z0, n1, in, twy); break;
+  }
+  __syncthreads();
+  switch (g.nx / team_lanes(g.nx)) {
+    case 2: passA_rows_inv<T, Epi, 2>(g, epi, tile, rs, z0, n1, twx); break;
+    case 4: passA_rows_inv<T, Epi, 4>(g, epi, tile, rs, z0, n1, twx); break;
+    default: passA_rows_inv<T, Epi, 8>(g, epi, tile, rs, z0, n1, twx); break;
+  }
+}
+
+// ---- pass B: outer y DFT + z FFT, spectral operator, inverse ---------------------------
+// Tile rows are (kxl, k1) pairs (row index kxl * Y1 + k1) of Nz values, row stride
+// pad16(Nz-1)+1.  Op supplies NI (intermediates transformed forward, 0..2),
+// combine(e, global index, wave, s0, s1) on the spectra (base left in s0) and nout
+// outputs out(o, base, wave), each inverse-transformed into outs.p[o].
+
+template <typename T, int Y, bool INV>
+__device__ __forceinline__ void passB_cols(const Geo& g, int kbn, const typename Cplx<T>::type* src,
+                                           long long cb, typename Cplx<T>::type* tile, int rs,
+                                           typename Cplx<T>::type* dst) {
+  using C = typename Cplx<T>::type;
+  const int ncols = kbn * g.nz;
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    const int kxl = col / g.nz, z = col - kxl * g.nz;
+    C v[Y > 1 ? Y : 1];
+    if (!INV) {
+#pragma unroll
+      for (int n1 = 0; n1 < Y; ++n1) v[n1] = src[cb + (long long)(kxl * Y + n1) * g.nz + z];
+      dftN<C, Y, false>(v);
+#pragma unroll
+      for (int k1 = 0; k1 < Y; ++k1) tile[(kxl * Y + k1) * rs + pad16(z)] = v[k1];
+    } else {
+#pragma unroll
+      for (int k1 = 0; k1 < Y; ++k1) v[k1] = tile[(kxl * Y + k1) * rs + pad16(z)];
+      dftN<C, Y, true>(v);
+#pragma unroll
+      for (int n1 = 0; n1 < Y; ++n1) dst[cb + (long long)(kxl * Y + n1) * g.nz + z] = v[n1];
+    }
+  }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void passB_cols_any(const Geo& g, int kbn, const typename Cplx<T>::type* src, long long cb,
+                                               typename Cplx<T>::type* tile, int rs, typename Cplx<T>::type* dst) {
+  switch (g.Y1) {
+    case 1: passB_cols<T, 1, INV>(g, kbn, src, cb, tile, rs, dst); break;
+    case 2: passB_cols<T, 2, INV>(g, kbn, src, cb, tile, rs, dst); break;
+    case 4: passB_cols<T, 4, INV>(g, kbn, src, cb, tile, rs, dst); break;
+    case 8: passB_cols<T, 8, INV>(g, kbn, src, cb, tile, rs, dst); break;
+    default: passB_cols<T, 16, INV>(g, kbn, src, cb, tile, rs, dst); break;
+  }
+}
+
+template <typename T, typename Op, int R>
+__device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, int k2, int kbn, long long cb,
+                                           typename Cplx<T>::type* tile0, typename Cplx<T>::type* tile1, int rs,
+                                           OutP<typename Cplx<T>::type> outs,
+                                           const typename Cplx<T>::type* __restrict__ twz) {
+  using C = typename Cplx<T>::type;
+  const int S = g.nz / R, lS = __ffs(S) - 1;
+  const int lane = threadIdx.x & 31, t = lane & (S - 1);
+  const int team = threadIdx.x / S, nteams = blockDim.x / S;
+  const int nrows = kbn * g.Y1;
+  const int br = bitrev_bits(t, lS);
+  // up to two rows per team, spectra kept in registers across the outputs
+  C base[2][R];
+  int rowid[2];
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int row = team + rr * nteams;
+    rowid[rr] = row;
+    const bool ok = row < nrows;
+    C s0[R], s1[R];
+    if (Op::NI >= 1) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) s0[j] = ok ? tile0[row * rs + pad16(t + S * j)] : C{0, 0};
+      team_fft<C, R, false>(s0, t, S, twz);
+    }
+    if (Op::NI >= 2) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) s1[j] = ok ? tile1[row * rs + pad16(t + S * j)] : C{0, 0};
+      team_fft<C, R, false>(s1, t, S, twz);
+    }
+    if (ok) {
+      const int kxl = row / g.Y1, k1 = row - kxl * g.Y1;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int kz = k + R * br;
+        const Wave w = make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz);
+        const int e = row * g.nz + kz;
+        op.combine(e, cb + e, w, s0[k], s1[k]);
+        base[rr][k] = s0[k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) base[rr][k] = C{0, 0};
+    }
+  }
+  __syncthreads();
+  for (int o = 0; o < op.nout; ++o) {
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int row = rowid[rr];
+      const bool ok = row < nrows;
+      C v[R];
+      const int kxl = ok ? row / g.Y1 : 0, k1 = ok ? row - kxl * g.Y1 : 0;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int kz = k + R * br;
+        v[k] = ok ? op.out(o, base[rr][k], make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz)) : C{0, 0};
+      }
+      team_fft<C, R, true>(v, t, S, twz);
+      if (ok) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) tile0[row * rs + pad16(t + S * j)] = v[j];
+      }
+    }
+    __syncthreads();
+    passB_cols_any<T, true>(g, kbn, nullptr, cb, tile0, rs, outs.p[o]);
+    __syncthreads();
+  }
 }
 
 template <typename T, typename Op>
-__global__ void __launch_bounds__(512) passB(Geo g, Op op, const typename Cplx<T>::type* __restrict__ in0,
+__global__ void __launch_bounds__(256) passB(Geo g, Op op, const typename Cplx<T>::type* __restrict__ in0,
                                              const typename Cplx<T>::type* __restrict__ in1,
                                              OutP<typename Cplx<T>::type> outs,
                                              const typename Cplx<T>::type* __restrict__ twy,
                                              const typename Cplx<T>::type* __restrict__ twz) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int slot = g.KB * g.Y1 * g.nz;
-  C* buf[3] = {reinterpret_cast<C*>(smem_raw), reinterpret_cast<C*>(smem_raw) + slot,
-               reinterpret_cast<C*>(smem_raw) + 2 * slot};
+  const int rs = pad16(g.nz - 1) + 1;
   const int kb = blockIdx.x / g.Y2, k2 = blockIdx.x % g.Y2;
   const int kx0 = kb * g.KB;
   const int kbn = min(g.KB, g.nxh - kx0);
-  const int cl = kbn * g.Y1 * g.nz;
   const long long cb = ((long long)(k2 * g.nxh + kx0) * g.Y1) * g.nz;
-  C* s0 = buf[0];
-  C* s1 = buf[1];
-  C* fr = buf[2];
-  if (Op::NI >= 1) {
-    for (int e = threadIdx.x; e < cl; e += blockDim.x) s0[e] = in0[cb + e];
-    __syncthreads();
-    C* r = passB_forward<C>(g, s0, fr, kbn, twy, twz);
-    if (r != s0) {
-      fr = s0;
-      s0 = r;
-    }
-  }
-  if (Op::NI >= 2) {
-    for (int e = threadIdx.x; e < cl; e += blockDim.x) s1[e] = in1[cb + e];
-    __syncthreads();
-    C* r = passB_forward<C>(g, s1, fr, kbn, twy, twz);
-    if (r != s1) {
-      fr = s1;
-      s1 = r;
-    }
-  }
-  const int per_kx = g.Y1 * g.nz;
-  for (int e = threadIdx.x; e < cl; e += blockDim.x) {
-    const int kxl = e / per_kx;
-    const int rem = e - kxl * per_kx;
-    const int k1 = rem / g.nz, kz = rem - k1 * g.nz;
-    const Wave w = make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz);
-    op.combine(e, cb + e, w, s0[e], s1[e]);
-  }
+  C* tile0 = reinterpret_cast<C*>(smem_raw);
+  C* tile1 = tile0 + (size_t)g.KB * g.Y1 * rs;
+  if (Op::NI >= 1) passB_cols_any<T, false>(g, kbn, in0, cb, tile0, rs, nullptr);
+  if (Op::NI >= 2) passB_cols_any<T, false>(g, kbn, in1, cb, tile1, rs, nullptr);
   __syncthreads();
-  for (int o = 0; o < op.nout; ++o) {
-    C* t = s1;
-    for (int e = threadIdx.x; e < cl; e += blockDim.x) {
-      const int kxl = e / per_kx;
-      const int rem = e - kxl * per_kx;
-      const int k1 = rem / g.nz, kz = rem - k1 * g.nz;
-      const Wave w = make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz);
-      t[e] = op.out(o, s0[e], w);
-    }
-    __syncthreads();
-    C* r = passB_inverse<C>(g, t, fr, kbn, twy, twz);
-    C* dst = outs.p[o];
-    for (int e = threadIdx.x; e < cl; e += blockDim.x) dst[cb + e] = r[e];
-    __syncthreads();
+  switch (g.nz / team_lanes(g.nz)) {
+    case 1: passB_rows<T, Op, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 2: passB_rows<T, Op, 2>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 4: passB_rows<T, Op, 4>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    default: passB_rows<T, Op, 8>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
   }
 }
 

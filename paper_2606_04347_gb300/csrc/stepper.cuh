@@ -241,7 +241,6 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
     int optin = 0;
     ETD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t budget = std::min<size_t>((size_t)optin, 200 * 1024);
     g_.dim = P_.dim;
     g_.nx = nx;
     g_.ny = ny;
@@ -257,25 +256,9 @@ template <typename T> class Stepper : public PlanBase {
     g_.hy = 2.0 * P_.half_len[1] / ny;
     g_.hz = P_.dim == 2 ? 1.0 : 2.0 * P_.half_len[2] / nz;
     hvol_ = g_.hx * g_.hy * (P_.dim == 2 ? 1.0 : g_.hz);
-    const size_t cs = sizeof(C);
-    g_.ZB = nz == 1 ? 1 : std::min(nz, cs == 8 ? 4 : 2);
-    g_.Y2 = 0;
-    for (int y2 = ny; y2 >= 2; y2 >>= 1) {
-      const int y1 = ny / y2;
-      const size_t a = 2 * (size_t)g_.ZB * y2 * g_.nxh * cs;
-      const size_t b = 3 * (size_t)y1 * nz * cs;
-      if (a <= budget && b <= budget) {
-        g_.Y2 = y2;
-        break;
-      }
-    }
-    if (!g_.Y2) throw Error(ETD_EINVAL, "grid too large for the two-pass FFT tiles");
-    g_.Y1 = ny / g_.Y2;
-    const size_t slot1 = (size_t)g_.Y1 * nz * cs;
-    g_.KB = (int)std::max<size_t>(1, std::min<size_t>((size_t)g_.nxh, (48 * 1024) / (3 * slot1)));
-    if (nz > 1) g_.KB = 1;
-    smemA_ = 2 * (size_t)g_.ZB * g_.Y2 * g_.nxh * cs;
-    smemB_ = 3 * (size_t)g_.KB * g_.Y1 * nz * cs;
+    if (!choose_tiles(g_, sizeof(C), smemA_, smemB1_))
+      throw Error(ETD_EINVAL, "grid not supported by the two-pass FFT tiles");
+    if ((size_t)optin < smemA_ || (size_t)optin < 2 * smemB1_) throw Error(ETD_EINVAL, "not enough shared memory");
 
     // model constants in the working precision
     mc_.eps_phi = (T)P_.eps_phi;
@@ -439,7 +422,7 @@ template <typename T> class Stepper : public PlanBase {
     auto k = passA_fwd<T, Pro>;
     set_smem((const void*)k, smemA_);
     timed(ETD_K_FFT_A_FWD, pro_reads(pro) * fld() + spc(), [&] {
-      k<<<(g_.nz / g_.ZB) * g_.Y1, 512, smemA_, st_>>>(g_, pro, out, twx_, twy_);
+      k<<<(g_.nz / g_.ZB) * g_.Y1, 256, smemA_, st_>>>(g_, pro, out, twx_, twy_);
     });
     ETD_CUDA(cudaGetLastError());
   }
@@ -448,7 +431,7 @@ template <typename T> class Stepper : public PlanBase {
     auto k = passA_inv<T, Epi>;
     set_smem((const void*)k, smemA_);
     timed(ETD_K_FFT_A_INV, spc() + epi_fields(epi) * fld(), [&] {
-      k<<<(g_.nz / g_.ZB) * g_.Y1, 512, smemA_, st_>>>(g_, in, epi, twx_, twy_);
+      k<<<(g_.nz / g_.ZB) * g_.Y1, 256, smemA_, st_>>>(g_, in, epi, twx_, twy_);
     });
     ETD_CUDA(cudaGetLastError());
   }
@@ -473,10 +456,11 @@ template <typename T> class Stepper : public PlanBase {
 
   template <typename Op> void passb(const Op& op, const C* in0, const C* in1, OutP<C> o) {
     auto k = passB<T, Op>;
-    set_smem((const void*)k, smemB_);
+    const size_t smemB = (Op::NI >= 2 ? 2 : 1) * smemB1_;
+    set_smem((const void*)k, smemB);
     const int nkb = (g_.nxh + g_.KB - 1) / g_.KB;
     timed(ETD_K_FFT_B, (Op::NI + op.nout + op_extra(op)) * spc(), [&] {
-      k<<<nkb * g_.Y2, 256, smemB_, st_>>>(g_, op, in0, in1, o, twy_, twz_);
+      k<<<nkb * g_.Y2, 256, smemB, st_>>>(g_, op, in0, in1, o, twy_, twz_);
     });
     ETD_CUDA(cudaGetLastError());
   }
@@ -898,7 +882,7 @@ template <typename T> class Stepper : public PlanBase {
   T c_lap_{};
   double hvol_ = 1.0;
   int nsm_ = 1;
-  size_t smemA_ = 0, smemB_ = 0;
+  size_t smemA_ = 0, smemB1_ = 0;
   std::vector<void*> allocs_;
   C* I_[5] = {};
   C *sphi_ = nullptr, *sS_ = nullptr, *sSu_ = nullptr;
