@@ -39,6 +39,7 @@ def _compile(src: str, extra) -> str:
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra) + (["-Xptxas", "-v"] if verbose else [])
+    extra += os.environ.get("ETD_NVCC_FLAGS", "").split()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"

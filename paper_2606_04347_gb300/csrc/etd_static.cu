@@ -107,11 +107,11 @@ etd_status run(int dim, const int* n, const void* field, void* half, cudaStream_
   auto kb = etd::passB<T, etd::OpToStd<T>>;
   if (smemA > 48 * 1024) cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
   if (smemB > 48 * 1024) cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
-  ka<<<(nz / g.ZB) * g.Y1, 256, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy);
+  ka<<<(nz / g.ZB) * g.Y1, ETD_PASSA_THREADS, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy);
   etd::OpToStd<T> op{0, static_cast<C*>(half), g.ny, g.nxh};
   etd::OutP<C> outs{};
   const int nkb = (g.nxh + g.KB - 1) / g.KB;
-  kb<<<nkb * g.Y2, 256, smemB, st>>>(g, op, I, nullptr, outs, twy, twz);
+  kb<<<nkb * g.Y2, ETD_PASSB_THREADS, smemB, st>>>(g, op, I, nullptr, outs, twy, twz);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     etd::set_last_error(std::string("launch: ") + cudaGetErrorString(e));

@@ -52,6 +52,24 @@ struct Geo {
   double hx, hy, hz;
 };
 
+// Launch shapes of the pass kernels (threads per CTA, CTAs per SM the FP32 register budget
+// is sized for; FP64 kernels keep the full register file) and the number of z-planes per pass-A tile in FP32 (FP64 uses half).
+#ifndef ETD_PASSA_THREADS
+#define ETD_PASSA_THREADS 256
+#endif
+#ifndef ETD_PASSA_MINB
+#define ETD_PASSA_MINB 4
+#endif
+#ifndef ETD_PASSB_THREADS
+#define ETD_PASSB_THREADS 256
+#endif
+#ifndef ETD_PASSB_MINB
+#define ETD_PASSB_MINB 2
+#endif
+#ifndef ETD_ZB32
+#define ETD_ZB32 2
+#endif
+
 // Shared-memory padding: one spare slot every 16 complex elements (bank spreading).
 __host__ __device__ __forceinline__ int pad16(int k) { return k + (k >> 4); }
 
@@ -64,7 +82,8 @@ inline bool choose_tiles(Geo& g, size_t csize, size_t& smemA, size_t& smemB1) {
   g.Y2 = g.ny < 16 ? g.ny : 16;
   g.Y1 = g.ny / g.Y2;
   if (g.Y1 > 16 || g.Y2 < 2) return false;
-  g.ZB = g.nz == 1 ? 1 : (g.nz < (csize == 8 ? 4 : 2) ? g.nz : (csize == 8 ? 4 : 2));
+  const int zb = csize == 8 ? ETD_ZB32 : (ETD_ZB32 > 1 ? ETD_ZB32 / 2 : 1);
+  g.ZB = g.nz == 1 ? 1 : (g.nz < zb ? g.nz : zb);
   const int rsa = pad16(g.nxh - 1) + 1;
   smemA = (size_t)g.ZB * g.Y2 * rsa * csize;
   if (g.nz > 1) {
@@ -317,7 +336,7 @@ __device__ __forceinline__ void passA_cols_fwd(const Geo& g, const typename Cplx
 }
 
 template <typename T, typename Pro>
-__global__ void __launch_bounds__(256) passA_fwd(Geo g, Pro pro, typename Cplx<T>::type* __restrict__ out,
+__global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_fwd(Geo g, Pro pro, typename Cplx<T>::type* __restrict__ out,
                                                  const typename Cplx<T>::type* __restrict__ twx,
                                                  const typename Cplx<T>::type* __restrict__ twy) {
   using C = typename Cplx<T>::type;
@@ -415,7 +434,7 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, con
 }
 
 template <typename T, typename Epi>
-__global__ void __launch_bounds__(256) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,
+__global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,
                                                  const typename Cplx<T>::type* __restrict__ twx,
                                                  const typename Cplx<T>::type* __restrict__ twy) {
   using C = typename Cplx<T>::type;
@@ -552,7 +571,7 @@ __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, 
 }
 
 template <typename T, typename Op>
-__global__ void __launch_bounds__(256) passB(Geo g, Op op, const typename Cplx<T>::type* __restrict__ in0,
+__global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_MINB : 1) passB(Geo g, Op op, const typename Cplx<T>::type* __restrict__ in0,
                                              const typename Cplx<T>::type* __restrict__ in1,
                                              OutP<typename Cplx<T>::type> outs,
                                              const typename Cplx<T>::type* __restrict__ twy,

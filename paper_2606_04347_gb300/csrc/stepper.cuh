@@ -422,7 +422,7 @@ template <typename T> class Stepper : public PlanBase {
     auto k = passA_fwd<T, Pro>;
     set_smem((const void*)k, smemA_);
     timed(ETD_K_FFT_A_FWD, pro_reads(pro) * fld() + spc(), [&] {
-      k<<<(g_.nz / g_.ZB) * g_.Y1, 256, smemA_, st_>>>(g_, pro, out, twx_, twy_);
+      k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smemA_, st_>>>(g_, pro, out, twx_, twy_);
     });
     ETD_CUDA(cudaGetLastError());
   }
@@ -431,7 +431,7 @@ template <typename T> class Stepper : public PlanBase {
     auto k = passA_inv<T, Epi>;
     set_smem((const void*)k, smemA_);
     timed(ETD_K_FFT_A_INV, spc() + epi_fields(epi) * fld(), [&] {
-      k<<<(g_.nz / g_.ZB) * g_.Y1, 256, smemA_, st_>>>(g_, in, epi, twx_, twy_);
+      k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smemA_, st_>>>(g_, in, epi, twx_, twy_);
     });
     ETD_CUDA(cudaGetLastError());
   }
@@ -460,7 +460,7 @@ template <typename T> class Stepper : public PlanBase {
     set_smem((const void*)k, smemB);
     const int nkb = (g_.nxh + g_.KB - 1) / g_.KB;
     timed(ETD_K_FFT_B, (Op::NI + op.nout + op_extra(op)) * spc(), [&] {
-      k<<<nkb * g_.Y2, 256, smemB, st_>>>(g_, op, in0, in1, o, twy_, twz_);
+      k<<<nkb * g_.Y2, ETD_PASSB_THREADS, smemB, st_>>>(g_, op, in0, in1, o, twy_, twz_);
     });
     ETD_CUDA(cudaGetLastError());
   }
