@@ -718,6 +718,7 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
   const T om = mg.omega, al = mg.alpha;
   for (int l = 0; l < mg.nlev - 1; ++l) {
     const MGL<T>& L = mg.L[l];
+    const MGL<T>& Cl = mg.L[l + 1];
     bool grid = l < mg.gl;
     int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
     if (!ps.step(grid, c)) return false;
@@ -735,8 +736,14 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
         L.e[i] = ei;
         r1out[i] = L.b[i] - s;
       }
+      if (mg.nu == 2) {  // the second sweep accumulates into the coarse right-hand side
+        const int Mc = *Cl.cnt;
+        for (int I = t0; I < Mc; I += ns) Cl.b[I] = 0;
+      }
     }
     if (mg.nu == 2) {
+      // second sweep e2 = e1 + w D^-1 r1, its residual r2 = r1 - w A D^-1 r1 added to the
+      // parent aggregate's right-hand side (the restriction of piecewise-constant P)
       if (!ps.step(grid, c)) return false;
       if (grid || blockIdx.x == 0) {
         const int M = *L.cnt;
@@ -749,11 +756,11 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
             s += L.c[f * L.cap + i] * (di - L.idg[j] * L.o[j]);
           }
           L.e[i] += om * di;
-          L.t[i] = L.o[i] - om * s;
+          atomicAdd(Cl.b + L.agg[i], L.o[i] - om * s);
         }
       }
+      continue;
     }
-    const MGL<T>& Cl = mg.L[l + 1];
     grid = (l + 1) < mg.gl;
     t0 = grid ? tid : threadIdx.x;
     ns = grid ? nth : blockDim.x;
