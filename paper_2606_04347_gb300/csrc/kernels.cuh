@@ -723,18 +723,25 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
     if (!ps.step(grid, c)) return false;
     if (grid || blockIdx.x == 0) {
-      T* r1out = mg.nu == 2 ? L.o : L.t;
-      const int M = *L.cnt;
+      T* __restrict__ r1out = mg.nu == 2 ? L.o : L.t;
+      const T* __restrict__ Lb = L.b;
+      const T* __restrict__ Lidg = L.idg;
+      const T* __restrict__ Lc = L.c;
+      const int* __restrict__ Lnb = L.nb;
+      T* __restrict__ Le = L.e;
+      const int M = *L.cnt, cap = L.cap;
+#pragma unroll 2
       for (int i = t0; i < M; i += ns) {
-        const T ei = om * L.idg[i] * L.b[i];
+        const T bi = Lb[i];
+        const T ei = om * Lidg[i] * bi;
         T s = 0;
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-          const int j = L.nb[f * L.cap + i];
-          s += L.c[f * L.cap + i] * (ei - om * L.idg[j] * L.b[j]);
+          const int j = Lnb[f * cap + i];
+          s += Lc[f * cap + i] * (ei - om * Lidg[j] * Lb[j]);
         }
-        L.e[i] = ei;
-        r1out[i] = L.b[i] - s;
+        Le[i] = ei;
+        r1out[i] = bi - s;
       }
       if (mg.nu == 2) {  // the second sweep accumulates into the coarse right-hand side
         const int Mc = *Cl.cnt;
@@ -746,17 +753,26 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
       // parent aggregate's right-hand side (the restriction of piecewise-constant P)
       if (!ps.step(grid, c)) return false;
       if (grid || blockIdx.x == 0) {
-        const int M = *L.cnt;
+        const T* __restrict__ Lo = L.o;
+        const T* __restrict__ Lidg = L.idg;
+        const T* __restrict__ Lc = L.c;
+        const int* __restrict__ Lnb = L.nb;
+        const int* __restrict__ Lagg = L.agg;
+        T* __restrict__ Le = L.e;
+        T* Cb = Cl.b;
+        const int M = *L.cnt, cap = L.cap;
+#pragma unroll 2
         for (int i = t0; i < M; i += ns) {
-          const T di = L.idg[i] * L.o[i];
+          const T oi = Lo[i];
+          const T di = Lidg[i] * oi;
           T s = 0;
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
-            const int j = L.nb[f * L.cap + i];
-            s += L.c[f * L.cap + i] * (di - L.idg[j] * L.o[j]);
+            const int j = Lnb[f * cap + i];
+            s += Lc[f * cap + i] * (di - Lidg[j] * Lo[j]);
           }
-          L.e[i] += om * di;
-          atomicAdd(Cl.b + L.agg[i], L.o[i] - om * s);
+          Le[i] += om * di;
+          atomicAdd(Cb + Lagg[i], oi - om * s);
         }
       }
       continue;
@@ -805,29 +821,50 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     if (!ps.step(grid, c)) return false;
     double acc = 0;
     if (grid || blockIdx.x == 0) {
-      T* out = mg.nu == 2 ? L.t : L.o;
-      const int M = *L.cnt;
+      T* __restrict__ out = mg.nu == 2 ? L.t : L.o;
+      const T* __restrict__ Le = L.e;
+      const T* __restrict__ Co = Cl.o;
+      const T* __restrict__ Lb = L.b;
+      const T* __restrict__ Lidg = L.idg;
+      const T* __restrict__ Lc = L.c;
+      const int* __restrict__ Lnb = L.nb;
+      const int* __restrict__ Lagg = L.agg;
+      const int M = *L.cnt, cap = L.cap;
+#pragma unroll 2
       for (int i = t0; i < M; i += ns) {
-        const T ei = L.e[i] + al * Cl.o[L.agg[i]];
+        const T ei = Le[i] + al * Co[Lagg[i]];
         T s = 0;
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-          const int j = L.nb[f * L.cap + i];
-          s += L.c[f * L.cap + i] * (ei - (L.e[j] + al * Cl.o[L.agg[j]]));
+          const int j = Lnb[f * cap + i];
+          s += Lc[f * cap + i] * (ei - (Le[j] + al * Co[Lagg[j]]));
         }
-        const T o1 = ei + om * L.idg[i] * (L.b[i] - s);
+        const T bi = Lb[i];
+        const T o1 = ei + om * Lidg[i] * (bi - s);
         out[i] = o1;
-        if (l == 0 && mg.nu == 1) acc += (double)L.b[i] * (double)o1;
+        if (l == 0 && mg.nu == 1) acc += (double)bi * (double)o1;
       }
     }
     if (mg.nu == 2) {
       if (!ps.step(grid, c)) return false;
       if (grid || blockIdx.x == 0) {
-        const int M = *L.cnt;
+        const T* __restrict__ Lt = L.t;
+        const T* __restrict__ Lb = L.b;
+        const T* __restrict__ Lidg = L.idg;
+        const T* __restrict__ Lc = L.c;
+        const int* __restrict__ Lnb = L.nb;
+        T* __restrict__ Lo = L.o;
+        const int M = *L.cnt, cap = L.cap;
+#pragma unroll 2
         for (int i = t0; i < M; i += ns) {
-          const T o2 = L.t[i] + om * L.idg[i] * (L.b[i] - mg_apply(L, L.t, i));
-          L.o[i] = o2;
-          if (l == 0) acc += (double)L.b[i] * (double)o2;
+          const T ti = Lt[i];
+          T s = 0;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) s += Lc[f * cap + i] * (ti - Lt[Lnb[f * cap + i]]);
+          const T bi = Lb[i];
+          const T o2 = ti + om * Lidg[i] * (bi - s);
+          Lo[i] = o2;
+          if (l == 0) acc += (double)bi * (double)o2;
         }
       }
     }
@@ -919,11 +956,18 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     const int par = k & 1;
     const T a = (T)alpha;
     double rrn = 0;
-    for (int i = tid; i < M; i += nth) {
-      v.x[i] += a * v.p[i];
-      const T r = v.r[i] - a * v.q[i];
-      v.r[i] = r;
-      rrn += (double)r * (double)r;
+    {
+      T* __restrict__ X = v.x;
+      T* __restrict__ Rr = v.r;
+      const T* __restrict__ P = v.p;
+      const T* __restrict__ Q = v.q;
+#pragma unroll 4
+      for (int i = tid; i < M; i += nth) {
+        X[i] += a * P[i];
+        const T r = Rr[i] - a * Q[i];
+        Rr[i] = r;
+        rrn += (double)r * (double)r;
+      }
     }
     block_add(rrn, c.acc + A_RR + par);
     if (!grid_sync(c)) return;
@@ -941,12 +985,23 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     const double beta = gnew / gamma;
     const T bt = (T)beta;
     double dun = 0;
-    for (int i = tid; i < M; i += nth) {
-      const T w = band_apply(v, v.u, i);
-      const T u = v.u[i];
-      v.p[i] = u + bt * v.p[i];
-      v.q[i] = w + bt * v.q[i];
-      dun += (double)w * (double)u;
+    {
+      const T* __restrict__ U = v.u;
+      const T* __restrict__ Cc = v.c;
+      const int* __restrict__ Nb = v.nb;
+      T* __restrict__ P = v.p;
+      T* __restrict__ Q = v.q;
+      const int cap = v.cap;
+#pragma unroll 2
+      for (int i = tid; i < M; i += nth) {
+        const T u = U[i];
+        T w = 0;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) w += Cc[f * cap + i] * (u - U[Nb[f * cap + i]]);
+        P[i] = u + bt * P[i];
+        Q[i] = w + bt * Q[i];
+        dun += (double)w * (double)u;
+      }
     }
     block_add(dun, c.acc + A_DU + par);
     if (!grid_sync(c)) return;
