@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=64, help="grid of the oracle sample")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=19, help="steps of the FP64 comparison leg (0: skip)")
     return ap.parse_args()
 
 
@@ -75,6 +76,36 @@ def allreduce_max(x: float, world: int) -> float:
 def aggregate(world: int, points: int, steps: int, ms_max: float) -> float:
     """Whole-job throughput in Mpoint-steps/s: units all replicas processed / slowest time."""
     return world * points * steps / (ms_max / 1e3) / 1e6
+
+
+def source_hash():
+    """sha256 over the CUDA sources: ties recorded ncu counters to the kernels they measured."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_04347_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kind, grid, prec):
+    """DRAM bytes per launch of a kernel class, from the committed ncu summary, if that summary
+    was taken on the kernels as they are now (same source hash); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic_c3.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for ln in f:
+            parts = ln.split()
+            if len(parts) == 2 and not ln.startswith("#"):
+                rec[parts[0]] = parts[1]
+    if rec.get("source_sha256") != source_hash():
+        return None
+    v = rec.get(f"{kind}_{grid}_{prec}")
+    return float(v) if v is not None else None
 
 
 def peaks():
@@ -236,6 +267,47 @@ def run_ours(a):
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
     launches = int(sum(v[1] for v in kt.values()))
 
+    # FP64 form of the same step on the same GPU (outside the timed region): speed-up of the
+    # FP32-mixed form and agreement of the two after the same number of steps
+    fp64 = None
+    if a.fp64_steps > 0 and prec == 1:
+        p64 = p.replace(precision=0, cg_rtol=1e-12)
+        plan64 = Plan(p64, stream=stream)
+        phi64 = torch.tensor(phi0, dtype=torch.float64, device="cuda")
+        u64 = torch.tensor(u0, dtype=torch.float64, device="cuda")
+        phi32 = torch.tensor(phi0, dtype=torch.float32, device="cuda")
+        u32 = torch.tensor(u0, dtype=torch.float32, device="cuda")
+        plan64.step(phi64, u64, 1)
+        plan.step(phi32, u32, 1)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        plan64.step(phi64, u64, a.fp64_steps)
+        f1.record(stream)
+        plan.step(phi32, u32, a.fp64_steps)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / a.fp64_steps
+        G = 18.0 * (phi64 * phi64 - phi64) ** 2
+
+        def rel(x, y, sel=None, wt=None):
+            x = x.double()
+            if sel is not None:
+                x, y = x[sel], y[sel]
+            if wt is not None:
+                return float(torch.sqrt((wt * (x - y) ** 2).sum() / (wt * y ** 2).sum()))
+            return float(torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(y))
+
+        d64 = plan64.energy(phi64, u64)
+        d32 = plan.energy(phi32, u32)
+        e64, e32 = d64["energy"], d32["energy"]
+        fp64 = {"ms_per_step": ms64, "value": npts / (ms64 / 1e3) / 1e6, "unit": UNIT,
+                "speedup_fp32_over_fp64": ms64 / (ms / a.steps), "steps_compared": a.fp64_steps + 1,
+                "rel_l2_phi": rel(phi32, phi64), "rel_l2_u_G": rel(u32, u64, wt=G),
+                "rel_l2_u": rel(u32, u64), "rel_l2_u_recovery": rel(u32, u64, G > p.recover_delta),
+                "rel_l2_u_core": rel(u32, u64, G > 0.1), "rel_energy": abs(e32 - e64) / abs(e64),
+                "max_bound_fp32": d32["max_bound"], "max_bound_fp64": d64["max_bound"]}
+        plan64.close()
+
     # end to end through the public API with host buffers
     esize = 4 if prec else 8
     h_phi = torch.from_numpy(phi0.astype(np.float32 if prec else np.float64)).pin_memory()
@@ -275,8 +347,10 @@ def run_ours(a):
                        "l2": "per-step traffic ~2 GB >> 129 MB L2: no flush needed",
                        "band_size": d["band_size"], "cg_iters_last": d["cg_iters_last"]},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
-                         "avg_launch_ms": dms / max(dn, 1)},
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": recorded_traffic(dom, a.size, a.precision),
+                         "algo_bytes_per_launch": dbytes / max(dn, 1), "avg_launch_ms": dms / max(dn, 1)},
+            "fp64_gpu": fp64,
             "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * npts * esize,
                     "d2h_bytes_per_step": 2 * npts * esize},

@@ -467,6 +467,7 @@ static __global__ void k_band_scatter(long long n, const unsigned char* __restri
 // (length M, band order), so every CG phase streams contiguous arrays.
 template <typename T> struct CGVec {
   T *x, *r, *u, *p, *q;   // compact vectors; q holds s = A p
+  T* r1;                  // second residual buffer (the multigrid iterations alternate r, r1)
   T* idg;                 // inverse diagonal
   T* c;                   // face coefficients, c[d * cap + i], d = x+, x-, y+, y-, z+, z-
   int* nb;                // compact index of the face neighbour (i itself when absent)
@@ -516,10 +517,10 @@ static __global__ void k_zero_left(const int* __restrict__ old_idx, const int* _
 
 template <typename T>
 __device__ __forceinline__ T band_apply(const CGVec<T>& v, const T* __restrict__ a, int i) {
-  const T ai = a[i];
+  const T ai = __ldcg(a + i);
   T s = 0;
 #pragma unroll
-  for (int f = 0; f < 6; ++f) s += v.c[f * v.cap + i] * (ai - a[v.nb[f * v.cap + i]]);
+  for (int f = 0; f < 6; ++f) s += v.c[f * v.cap + i] * (ai - __ldcg(a + v.nb[f * v.cap + i]));
   return s;
 }
 
@@ -542,7 +543,7 @@ template <typename T> struct RhsGF {  // G f(u): fixed-model operand (Eq. (2.16)
 
 struct CGCtl {
   double* acc;          // 16 FP64 accumulators (zeroed before launch)
-  unsigned* bar;        // [0] arrival count, [1] generation
+  unsigned* bar;        // [0] monotonic arrival count
   int* status;          // plan status word
   int* iters;           // out: iterations
   double* resid;        // out: relative residual
@@ -552,24 +553,42 @@ struct CGCtl {
   unsigned long long* work;  // accumulates band nodes x sweeps (measurement)
 };
 
-// Grid-wide barrier for a cooperative launch.  The spin has a clock budget: when it runs
-// out the kernel records ETD_ETIMEOUT in the status word and every block returns at its
-// next check.  Returns false once the status is non-zero.
+// Inside the band CG kernel every vector that the kernel itself writes (x, r, u, p, q and
+// the multigrid levels' b, e, o, t) is read with __ldcg: an L2 load, never the read-only
+// path that a const __restrict__ pointer would allow, which is only valid for data that no
+// thread writes during the launch.  The couplings, neighbour lists and level maps are built
+// by earlier launches and are read normally.
+
+// Grid-wide barrier for a cooperative launch on one monotonic arrival counter (zeroed
+// before the launch): barrier number e completes when the counter reaches e * gridDim.x,
+// and each block learns e from the value its own arrival returned, so nothing is reset
+// between barriers.  The block's writes are published by the block barrier followed by an
+// acquire-release add at GPU scope; blocks that arrive early poll with acquire loads, and
+// the last one to arrive takes its acquire from the add itself (without it, its L1 could
+// still hold lines that other blocks rewrote during the phase).  The spin has a
+// clock budget: when it runs out the kernel records ETD_ETIMEOUT in the status word and
+// every block returns at its next check.  Returns false once the status is non-zero.
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_sync(const CGCtl& c) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = c.bar + 1;
-    const unsigned my = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(c.bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(c.bar, 0u);
-      __threadfence();
-      atomicAdd(c.bar + 1, 1u);
-    } else {
+    const unsigned nb = gridDim.x;
+    const unsigned old = atom_add_acq_rel_gpu(c.bar, 1u);
+    const unsigned target = (old / nb + 1u) * nb;
+    if (old + 1u != target) {
       const long long t0 = clock64();
-      while (*gen == my) {
+      while ((int)(ld_acquire_gpu(c.bar) - target) < 0) {
         if (clock64() - t0 > c.budget) {
           atomicCAS(c.status, 0, 6);
           break;
@@ -577,7 +596,6 @@ __device__ __forceinline__ bool grid_sync(const CGCtl& c) {
         __nanosleep(32);
       }
     }
-    __threadfence();
     ok = (*(volatile int*)c.status == 0);
   }
   __syncthreads();
@@ -681,10 +699,10 @@ __global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict
 }
 
 template <typename T> __device__ __forceinline__ T mg_apply(const MGL<T>& L, const T* __restrict__ v, int i) {
-  const T vi = v[i];
+  const T vi = __ldcg(v + i);
   T s = 0;
 #pragma unroll
-  for (int f = 0; f < 6; ++f) s += L.c[f * L.cap + i] * (vi - v[L.nb[f * L.cap + i]]);
+  for (int f = 0; f < 6; ++f) s += L.c[f * L.cap + i] * (vi - __ldcg(v + L.nb[f * L.cap + i]));
   return s;
 }
 
@@ -706,42 +724,93 @@ struct PhaseSync {
   }
 };
 
-// u = V(r), one symmetric V(nu,nu) cycle (nu = 1 or 2 weighted-Jacobi sweeps before and
-// after the coarse-grid correction, which is scaled by alpha).  On entry r (level-0 b) is
-// complete and visible; on return every block has written its share of u (level-0 o) and
-// added its part of (r,u) to *ru.  Residuals of the pre-sweeps are carried algebraically:
-// e1 = w D^-1 b, r1 = b - A e1 (needs b at the neighbours), e2 = e1 + w D^-1 r1,
-// r2 = r1 - w A D^-1 r1 (needs r1 at the neighbours).  Returns false if a barrier failed.
-template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c, double* ru) {
+// The CG update x += a p, r_new = r_old - a q folded into the first smoothing sweep of the
+// V-cycle that preconditions r_new (the sweep needs r_new at the neighbours, which it
+// recomputes from r_old and q there, so the separate update pass and its barrier go away).
+template <typename T> struct CGFuse {
+  bool on;
+  const T* rold;
+  T* x;
+  const T* p;
+  const T* q;
+  T a;
+  double* rr;       // accumulates (r_new, r_new)
+  double tol2;      // stop when (r_new, r_new) <= tol2
+  double* zero;     // a CG accumulator every block has finished reading: zeroed on the way
+};
+
+// u = V(b), one symmetric V(nu,nu) cycle (nu = 1 or 2 weighted-Jacobi sweeps before and
+// after the coarse-grid correction, which is scaled by alpha) for the level-0 right-hand
+// side b.  On entry b is complete and visible (or, with the fused CG update, r_old, q, p and
+// x are); on return every block has written its share of u (level-0 o) and added its part of
+// (b,u) to *ru.  Residuals of the pre-sweeps are carried algebraically: e1 = w D^-1 b,
+// r1 = b - A e1 (needs b at the neighbours), e2 = e1 + w D^-1 r1, r2 = r1 - w A D^-1 r1
+// (needs r1 at the neighbours).  Returns -1 if a barrier failed, 1 if the fused update met
+// the tolerance (the cycle is abandoned, *rr_out holds (r_new, r_new)), else 0.
+template <typename T>
+__device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __restrict__ b0, const CGFuse<T>& F, double* ru,
+                         double* rr_out) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   PhaseSync ps{true, true};
   const T om = mg.omega, al = mg.alpha;
+  // after the barrier that follows the fused sweep: every block sees (r_new, r_new)
+  auto fused_check = [&]() -> bool {
+    const double rr = *(volatile double*)F.rr;
+    *rr_out = rr;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *F.zero = 0.0;
+    return rr <= F.tol2;
+  };
   for (int l = 0; l < mg.nlev - 1; ++l) {
     const MGL<T>& L = mg.L[l];
     const MGL<T>& Cl = mg.L[l + 1];
     bool grid = l < mg.gl;
     int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
-    if (!ps.step(grid, c)) return false;
+    if (!ps.step(grid, c)) return -1;
     if (grid || blockIdx.x == 0) {
       T* __restrict__ r1out = mg.nu == 2 ? L.o : L.t;
-      const T* __restrict__ Lb = L.b;
       const T* __restrict__ Lidg = L.idg;
       const T* __restrict__ Lc = L.c;
       const int* __restrict__ Lnb = L.nb;
       T* __restrict__ Le = L.e;
       const int M = *L.cnt, cap = L.cap;
-#pragma unroll 2
-      for (int i = t0; i < M; i += ns) {
-        const T bi = Lb[i];
-        const T ei = om * Lidg[i] * bi;
-        T s = 0;
+      if (l == 0 && F.on) {
+        const T* __restrict__ Ro = F.rold;
+        const T* __restrict__ Q = F.q;
+        const T* __restrict__ P = F.p;
+        T* __restrict__ X = F.x;
+        const T a = F.a;
+        double rr = 0;
+        for (int i = t0; i < M; i += ns) {
+          const T bi = __ldcg(Ro + i) - a * __ldcg(Q + i);
+          X[i] = __ldcg(X + i) + a * __ldcg(P + i);
+          b0[i] = bi;
+          rr += (double)bi * (double)bi;
+          const T ei = om * Lidg[i] * bi;
+          T s = 0;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-          const int j = Lnb[f * cap + i];
-          s += Lc[f * cap + i] * (ei - om * Lidg[j] * Lb[j]);
+          for (int f = 0; f < 6; ++f) {
+            const int j = Lnb[f * cap + i];
+            s += Lc[f * cap + i] * (ei - om * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
+          }
+          Le[i] = ei;
+          r1out[i] = bi - s;
         }
-        Le[i] = ei;
-        r1out[i] = bi - s;
+        block_add(rr, F.rr);
+      } else {
+        const T* __restrict__ Lb = l == 0 ? b0 : L.b;
+#pragma unroll 2
+        for (int i = t0; i < M; i += ns) {
+          const T bi = __ldcg(Lb + i);
+          const T ei = om * Lidg[i] * bi;
+          T s = 0;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            const int j = Lnb[f * cap + i];
+            s += Lc[f * cap + i] * (ei - om * Lidg[j] * __ldcg(Lb + j));
+          }
+          Le[i] = ei;
+          r1out[i] = bi - s;
+        }
       }
       if (mg.nu == 2) {  // the second sweep accumulates into the coarse right-hand side
         const int Mc = *Cl.cnt;
@@ -751,7 +820,8 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     if (mg.nu == 2) {
       // second sweep e2 = e1 + w D^-1 r1, its residual r2 = r1 - w A D^-1 r1 added to the
       // parent aggregate's right-hand side (the restriction of piecewise-constant P)
-      if (!ps.step(grid, c)) return false;
+      if (!ps.step(grid, c)) return -1;
+      if (l == 0 && F.on && fused_check()) return 1;
       if (grid || blockIdx.x == 0) {
         const T* __restrict__ Lo = L.o;
         const T* __restrict__ Lidg = L.idg;
@@ -763,15 +833,15 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
         const int M = *L.cnt, cap = L.cap;
 #pragma unroll 2
         for (int i = t0; i < M; i += ns) {
-          const T oi = Lo[i];
+          const T oi = __ldcg(Lo + i);
           const T di = Lidg[i] * oi;
           T s = 0;
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += Lc[f * cap + i] * (di - Lidg[j] * Lo[j]);
+            s += Lc[f * cap + i] * (di - Lidg[j] * __ldcg(Lo + j));
           }
-          Le[i] += om * di;
+          Le[i] = __ldcg(Le + i) + om * di;
           atomicAdd(Cb + Lagg[i], oi - om * s);
         }
       }
@@ -780,7 +850,8 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     grid = (l + 1) < mg.gl;
     t0 = grid ? tid : threadIdx.x;
     ns = grid ? nth : blockDim.x;
-    if (!ps.step(grid, c)) return false;
+    if (!ps.step(grid, c)) return -1;
+    if (l == 0 && F.on && fused_check()) return 1;
     if (grid || blockIdx.x == 0) {
       const int M = *Cl.cnt;
       for (int I = t0; I < M; I += ns) {
@@ -788,7 +859,7 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = Cl.child[q * Cl.cap + I];
-          if (j >= 0) s += L.t[j];
+          if (j >= 0) s += __ldcg(L.t + j);
         }
         Cl.b[I] = s;
       }
@@ -798,18 +869,18 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     const MGL<T>& L = mg.L[mg.nlev - 1];
     const bool grid = (mg.nlev - 1) < mg.gl;
     const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
-    if (!ps.step(grid, c)) return false;
+    if (!ps.step(grid, c)) return -1;
     if (grid || blockIdx.x == 0) {
       const int M = *L.cnt;
-      for (int i = t0; i < M; i += ns) L.e[i] = om * L.idg[i] * L.b[i];
+      for (int i = t0; i < M; i += ns) L.e[i] = om * L.idg[i] * __ldcg(L.b + i);
     }
     for (int s = 1; s < mg.csweeps; ++s) {
-      if (!ps.step(grid, c)) return false;
+      if (!ps.step(grid, c)) return -1;
       const T* src = (s & 1) ? L.e : L.o;
       T* dst = (s & 1) ? L.o : L.e;
       if (grid || blockIdx.x == 0) {
         const int M = *L.cnt;
-        for (int i = t0; i < M; i += ns) dst[i] = src[i] + om * L.idg[i] * (L.b[i] - mg_apply(L, src, i));
+        for (int i = t0; i < M; i += ns) dst[i] = __ldcg(src + i) + om * L.idg[i] * (__ldcg(L.b + i) - mg_apply(L, src, i));
       }
     }
   }
@@ -818,13 +889,13 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     const MGL<T>& Cl = mg.L[l + 1];
     const bool grid = l < mg.gl;
     const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
-    if (!ps.step(grid, c)) return false;
+    if (!ps.step(grid, c)) return -1;
     double acc = 0;
     if (grid || blockIdx.x == 0) {
       T* __restrict__ out = mg.nu == 2 ? L.t : L.o;
       const T* __restrict__ Le = L.e;
       const T* __restrict__ Co = Cl.o;
-      const T* __restrict__ Lb = L.b;
+      const T* __restrict__ Lb = l == 0 ? b0 : L.b;
       const T* __restrict__ Lidg = L.idg;
       const T* __restrict__ Lc = L.c;
       const int* __restrict__ Lnb = L.nb;
@@ -832,24 +903,24 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
       const int M = *L.cnt, cap = L.cap;
 #pragma unroll 2
       for (int i = t0; i < M; i += ns) {
-        const T ei = Le[i] + al * Co[Lagg[i]];
+        const T ei = __ldcg(Le + i) + al * __ldcg(Co + Lagg[i]);
         T s = 0;
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           const int j = Lnb[f * cap + i];
-          s += Lc[f * cap + i] * (ei - (Le[j] + al * Co[Lagg[j]]));
+          s += Lc[f * cap + i] * (ei - (__ldcg(Le + j) + al * __ldcg(Co + Lagg[j])));
         }
-        const T bi = Lb[i];
+        const T bi = __ldcg(Lb + i);
         const T o1 = ei + om * Lidg[i] * (bi - s);
         out[i] = o1;
         if (l == 0 && mg.nu == 1) acc += (double)bi * (double)o1;
       }
     }
     if (mg.nu == 2) {
-      if (!ps.step(grid, c)) return false;
+      if (!ps.step(grid, c)) return -1;
       if (grid || blockIdx.x == 0) {
         const T* __restrict__ Lt = L.t;
-        const T* __restrict__ Lb = L.b;
+        const T* __restrict__ Lb = l == 0 ? b0 : L.b;
         const T* __restrict__ Lidg = L.idg;
         const T* __restrict__ Lc = L.c;
         const int* __restrict__ Lnb = L.nb;
@@ -857,11 +928,11 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
         const int M = *L.cnt, cap = L.cap;
 #pragma unroll 2
         for (int i = t0; i < M; i += ns) {
-          const T ti = Lt[i];
+          const T ti = __ldcg(Lt + i);
           T s = 0;
 #pragma unroll
-          for (int f = 0; f < 6; ++f) s += Lc[f * cap + i] * (ti - Lt[Lnb[f * cap + i]]);
-          const T bi = Lb[i];
+          for (int f = 0; f < 6; ++f) s += Lc[f * cap + i] * (ti - __ldcg(Lt + Lnb[f * cap + i]));
+          const T bi = __ldcg(Lb + i);
           const T o2 = ti + om * Lidg[i] * (bi - s);
           Lo[i] = o2;
           if (l == 0) acc += (double)bi * (double)o2;
@@ -870,21 +941,27 @@ template <typename T> __device__ bool mg_vcycle(const MGP<T>& mg, const CGCtl& c
     }
     if (l == 0) block_add(acc, ru);
   }
-  return true;
+  return 0;
 }
 
 enum { A_SUMF = 0, A_BB = 1, A_RU0 = 2, A_RR0 = 3, A_DU0 = 4, A_RU = 5, A_RR = 7, A_DU = 9, A_SUMX = 11 };
 
-// u = M^{-1} r with M = Jacobi (one level) or one multigrid V-cycle; adds (r,u) to *ru.
+// u = M^{-1} b with M = Jacobi (one level) or one multigrid V-cycle; adds (b,u) to *ru.
 template <typename T>
-__device__ __forceinline__ bool precond(const CGVec<T>& v, const MGP<T>& mg, const CGCtl& c, int M, double* ru) {
-  if (mg.nlev > 1) return mg_vcycle(mg, c, ru);
+__device__ __forceinline__ bool precond(const CGVec<T>& v, const MGP<T>& mg, const CGCtl& c, int M, T* b,
+                                        double* ru) {
+  if (mg.nlev > 1) {
+    CGFuse<T> off{};
+    double rr;
+    return mg_vcycle(mg, c, b, off, ru, &rr) == 0;
+  }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   double acc = 0;
   for (int i = tid; i < M; i += nth) {
-    const T u = v.r[i] * v.idg[i];
+    const T bi = __ldcg(b + i);
+    const T u = bi * v.idg[i];
     v.u[i] = u;
-    acc += (double)v.r[i] * (double)u;
+    acc += (double)bi * (double)u;
   }
   block_add(acc, ru);
   return true;
@@ -896,6 +973,9 @@ __device__ __forceinline__ bool precond(const CGVec<T>& v, const MGP<T>& mg, con
 //   u = M^{-1} r, gamma = (r,u)                       | barrier
 //   B: w = A u, p = u + b p, s = w + b s, delta=(w,u) | barrier
 //   b = gamma/gamma_old, a = gamma/(delta - b gamma/a_old)
+// With the multigrid preconditioner, A is folded into the first sweep of the V-cycle and
+// the residual alternates between two buffers (the sweep reads the old one at the
+// neighbours while it writes the new one).
 template <typename T, typename Rhs>
 __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, const int* __restrict__ count,
                                                 CGVec<T> v, T* __restrict__ wfull, Rhs rhs, CGCtl c, MGP<T> mg) {
@@ -912,14 +992,16 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
   for (int i = tid; i < M; i += nth) {
     const int p = idx[i];
     v.x[i] = wfull[p];          // warm start from the previous solution
-    s += rhs(p);
+    const double f = rhs(p);
+    v.r1[i] = (T)f;             // f kept for the residual pass
+    s += f;
   }
   block_add(s, c.acc + A_SUMF);
   if (!grid_sync(c)) return;
   const double meanf = *(volatile double*)(c.acc + A_SUMF) / M;
   double bb = 0, rr = 0;
   for (int i = tid; i < M; i += nth) {
-    const double b = rhs(idx[i]) - meanf;
+    const double b = (double)__ldcg(v.r1 + i) - meanf;
     const T r = (T)(b - (double)band_apply(v, v.x, i));
     v.r[i] = r;
     bb += b * b;
@@ -934,13 +1016,13 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
   bool conv = (bb == 0.0) || (rr <= tol2);
   double gamma = 0, delta = 0, alpha = 0;
   if (!conv) {
-    if (!precond(v, mg, c, M, c.acc + A_RU0)) return;
+    if (!precond(v, mg, c, M, v.r, c.acc + A_RU0)) return;
     if (!grid_sync(c)) return;
     gamma = *(volatile double*)(c.acc + A_RU0);
     double du = 0;
     for (int i = tid; i < M; i += nth) {
       const T w = band_apply(v, v.u, i);
-      const T u = v.u[i];
+      const T u = __ldcg(v.u + i);
       v.p[i] = u;
       v.q[i] = w;
       du += (double)w * (double)u;
@@ -951,34 +1033,46 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     if (!(delta > 0.0)) conv = true;
     alpha = conv ? 0.0 : gamma / delta;
   }
+  const bool fuse = mg.nlev > 1;
   int k = 0;
   while (!conv && k < c.maxit) {
     const int par = k & 1;
     const T a = (T)alpha;
-    double rrn = 0;
-    {
-      T* __restrict__ X = v.x;
-      T* __restrict__ Rr = v.r;
-      const T* __restrict__ P = v.p;
-      const T* __restrict__ Q = v.q;
-#pragma unroll 4
-      for (int i = tid; i < M; i += nth) {
-        X[i] += a * P[i];
-        const T r = Rr[i] - a * Q[i];
-        Rr[i] = r;
-        rrn += (double)r * (double)r;
+    if (fuse) {
+      CGFuse<T> F{true, par ? v.r1 : v.r, v.x, v.p, v.q, a, c.acc + A_RR + par, tol2, c.acc + A_DU + (par ^ 1)};
+      const int st = mg_vcycle(mg, c, par ? v.r : v.r1, F, c.acc + A_RU + par, &rr);
+      if (st < 0) return;
+      ++k;
+      if (st == 1) {
+        conv = true;
+        break;
       }
+    } else {
+      double rrn = 0;
+      {
+        T* __restrict__ X = v.x;
+        T* __restrict__ Rr = v.r;
+        const T* __restrict__ P = v.p;
+        const T* __restrict__ Q = v.q;
+#pragma unroll 4
+        for (int i = tid; i < M; i += nth) {
+          X[i] = __ldcg(X + i) + a * __ldcg(P + i);
+          const T r = __ldcg(Rr + i) - a * __ldcg(Q + i);
+          Rr[i] = r;
+          rrn += (double)r * (double)r;
+        }
+      }
+      block_add(rrn, c.acc + A_RR + par);
+      if (!grid_sync(c)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_DU + (par ^ 1)] = 0.0;
+      rr = *(volatile double*)(c.acc + A_RR + par);
+      ++k;
+      if (rr <= tol2) {
+        conv = true;
+        break;
+      }
+      if (!precond(v, mg, c, M, v.r, c.acc + A_RU + par)) return;
     }
-    block_add(rrn, c.acc + A_RR + par);
-    if (!grid_sync(c)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_DU + (par ^ 1)] = 0.0;
-    rr = *(volatile double*)(c.acc + A_RR + par);
-    ++k;
-    if (rr <= tol2) {
-      conv = true;
-      break;
-    }
-    if (!precond(v, mg, c, M, c.acc + A_RU + par)) return;
     if (!grid_sync(c)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_RR + par] = 0.0;
     const double gnew = *(volatile double*)(c.acc + A_RU + par);
@@ -994,12 +1088,12 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
       const int cap = v.cap;
 #pragma unroll 2
       for (int i = tid; i < M; i += nth) {
-        const T u = U[i];
+        const T u = __ldcg(U + i);
         T w = 0;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) w += Cc[f * cap + i] * (u - U[Nb[f * cap + i]]);
-        P[i] = u + bt * P[i];
-        Q[i] = w + bt * Q[i];
+        for (int f = 0; f < 6; ++f) w += Cc[f * cap + i] * (u - __ldcg(U + Nb[f * cap + i]));
+        P[i] = u + bt * __ldcg(P + i);
+        Q[i] = w + bt * __ldcg(Q + i);
         dun += (double)w * (double)u;
       }
     }
@@ -1015,11 +1109,11 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
   // zero-mean projection of the solution (single band component)
   if (!grid_sync(c)) return;
   double sx = 0;
-  for (int i = tid; i < M; i += nth) sx += (double)v.x[i];
+  for (int i = tid; i < M; i += nth) sx += (double)__ldcg(v.x + i);
   block_add(sx, c.acc + A_SUMX);
   if (!grid_sync(c)) return;
   const T mx = (T)(*(volatile double*)(c.acc + A_SUMX) / M);
-  for (int i = tid; i < M; i += nth) wfull[idx[i]] = v.x[i] - mx;
+  for (int i = tid; i < M; i += nth) wfull[idx[i]] = __ldcg(v.x + i) - mx;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *c.iters = k;
     *c.resid = bb > 0 ? sqrt(rr / bb) : 0.0;

@@ -294,7 +294,7 @@ template <typename T> class Stepper : public PlanBase {
     sS_ = alloc<C>(g_.nhat);
     sSu_ = alloc<C>(g_.nhat);
     T** reals[] = {&phiA_, &phiB_, &phit_, &lap_, &gx_, &gy_, &gz_, &lu_, &rr_, &wm_, &r2_, &ut_, &G_, &w_,
-                   &cg_.x, &cg_.r, &cg_.u, &cg_.p, &cg_.q, &cg_.idg};
+                   &cg_.x, &cg_.r, &cg_.r1, &cg_.u, &cg_.p, &cg_.q, &cg_.idg};
     for (T** r : reals) *r = alloc<T>(g_.n);
     for (T** r : reals) ETD_CUDA(cudaMemset(*r, 0, sizeof(T) * g_.n));
     cg_.cap = (int)g_.n;
