@@ -137,13 +137,19 @@ template <typename T> struct EpiStore {
   __device__ void operator()(long long i, T v) const { out[i] = v; }
 };
 // U = GU/G where G > delta, GU elsewhere (Sec. 3.3, recovery after Algorithm 1).
+// u from the increment of G u over a stage: the inverse transform delivers
+// d = GU_new - G u_base, and on the recovery set {G > delta} u = GU_new / G is formed as
+// u_base + d / G (equal in exact arithmetic; the FP32 transform error then scales with the
+// increment instead of with G u itself), elsewhere u = GU_new = G u_base + d (Algorithm 1).
 template <typename T> struct EpiRecover {
   T* out;
   const T* G;
+  const T* base;
   T delta;
   __device__ void operator()(long long i, T v) const {
     const T gg = G[i];
-    out[i] = gg > delta ? v / gg : v;
+    const T ub = base[i];
+    out[i] = gg > delta ? ub + v / gg : gg * ub + v;
   }
 };
 // phi^{n+1} and G^{n+1} = 18 (phi^2 - phi)^2 (Algorithm 1).
@@ -976,9 +982,20 @@ __device__ __forceinline__ bool precond(const CGVec<T>& v, const MGP<T>& mg, con
 // With the multigrid preconditioner, A is folded into the first sweep of the V-cycle and
 // the residual alternates between two buffers (the sweep reads the old one at the
 // neighbours while it writes the new one).
+// Initial guess of a band solve, x0 = a + cb b + cc c over the band (b, c may be null), from
+// earlier solutions kept on the full grid; the solution is also written to hist (if set).
+template <typename T> struct CGGuess {
+  const T* a;
+  const T* b;
+  const T* c;
+  T cb, cc;
+  T* hist;
+};
+
 template <typename T, typename Rhs>
 __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, const int* __restrict__ count,
-                                                CGVec<T> v, T* __restrict__ wfull, Rhs rhs, CGCtl c, MGP<T> mg) {
+                                                CGVec<T> v, T* __restrict__ wfull, Rhs rhs, CGCtl c, MGP<T> mg,
+                                                CGGuess<T> gs) {
   const int M = *count;
   if (M == 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -991,7 +1008,10 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
   double s = 0;
   for (int i = tid; i < M; i += nth) {
     const int p = idx[i];
-    v.x[i] = wfull[p];          // warm start from the previous solution
+    T x0 = gs.a[p];
+    if (gs.b) x0 += gs.cb * gs.b[p];
+    if (gs.c) x0 += gs.cc * gs.c[p];
+    v.x[i] = x0;
     const double f = rhs(p);
     v.r1[i] = (T)f;             // f kept for the residual pass
     s += f;
@@ -1113,7 +1133,12 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
   block_add(sx, c.acc + A_SUMX);
   if (!grid_sync(c)) return;
   const T mx = (T)(*(volatile double*)(c.acc + A_SUMX) / M);
-  for (int i = tid; i < M; i += nth) wfull[idx[i]] = __ldcg(v.x + i) - mx;
+  for (int i = tid; i < M; i += nth) {
+    const int p = idx[i];
+    const T w = __ldcg(v.x + i) - mx;
+    wfull[p] = w;
+    if (gs.hist) gs.hist[p] = w;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *c.iters = k;
     *c.resid = bb > 0 ? sqrt(rr / bb) : 0.0;

@@ -3,7 +3,8 @@
 // Coefficient table (built in FP64 on the host, Sec. 2.2 phi-functions of Sec. 3.2
 // symbols): for every integer m = |k|^2 of the cubic box, 6 entries
 //   tab[6m + 0..2] = phi0, tau phi1, tau phi2 at z = tau l^phi(lambda_m)
-//   tab[6m + 3..5] = phi0, tau phi1, tau phi2 at z = tau l^u(lambda_m)
+//   tab[6m + 3..5] = phi0 - 1, tau phi1, tau phi2 at z = tau l^u(lambda_m)
+// (phi0 - 1 = expm1(-z): the u-stage transforms the increment of G u, see OpUPred)
 // with lambda_m = -(pi/X)^2 m.
 #pragma once
 #include "fft.cuh"
@@ -102,7 +103,8 @@ template <typename T> struct OpPhiCorr {
   __device__ C out(int, C v, const Wave&) const { return cscale(v, k.inv_n); }
 };
 
-// u-stage predictor: GU~^ = phi0 FFT(G u^n) + tau phi1 R2^ ; RK2 stores S = GU~^ - tau phi2 R2^.
+// u-stage predictor as an increment: D~^ = GU~^ - FFT(G u^n) = (phi0 - 1) FFT(G u^n) + tau phi1 R2^,
+// so that GU~ = G u^n + IFFT(D~^) (EpiRecover adds G u^n back); RK2 stores S = D~^ - tau phi2 R2^.
 template <typename T> struct OpUPred {
   using C = typename Cplx<T>::type;
   static constexpr int NI = 2;
@@ -119,7 +121,7 @@ template <typename T> struct OpUPred {
   __device__ C out(int, C v, const Wave&) const { return cscale(v, k.inv_n); }
 };
 
-// u-stage corrector: GU^{n+1}^ = S + tau phi2 R2(U~)^.
+// u-stage corrector: GU^{n+1}^ - FFT(G u^n) = S + tau phi2 R2(U~)^.
 template <typename T> struct OpUCorr {
   using C = typename Cplx<T>::type;
   static constexpr int NI = 1;

@@ -301,6 +301,10 @@ template <typename T> class Stepper : public PlanBase {
     cg_.c = alloc<T>(6 * (size_t)g_.n);
     cg_.nb = alloc<int>(6 * (size_t)g_.n);
     bmap_ = alloc<int>(g_.n);
+    for (T*& h : hs_) {
+      h = alloc<T>(g_.n);
+      ETD_CUDA(cudaMemset(h, 0, sizeof(T) * g_.n));
+    }
     init_multigrid();
     mask_ = alloc<unsigned char>(g_.n);
     idx_ = alloc<int>(g_.n);
@@ -346,7 +350,7 @@ template <typename T> class Stepper : public PlanBase {
       t[0] = (T)a0;
       t[1] = (T)(P_.tau * a1);
       t[2] = (T)(P_.tau * a2);
-      t[3] = (T)b0;
+      t[3] = (T)std::expm1(-P_.tau * lu);  // phi0 - 1: the u-stage is advanced as an increment
       t[4] = (T)(P_.tau * b1);
       t[5] = (T)(P_.tau * b2);
     }
@@ -415,7 +419,7 @@ template <typename T> class Stepper : public PlanBase {
   static int pro_reads(const ProLoad<T>&) { return 1; }
   static int pro_reads(const ProMul<T>&) { return 2; }
   static int epi_fields(const EpiStore<T>&) { return 1; }
-  static int epi_fields(const EpiRecover<T>&) { return 2; }
+  static int epi_fields(const EpiRecover<T>&) { return 3; }
   static int epi_fields(const EpiPhiG<T>&) { return 2; }
 
   template <typename Pro> void fwd(Pro pro, C* out) {
@@ -508,7 +512,46 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaGetLastError());
   }
 
-  template <typename Rhs> void cg_solve(Rhs rhs, T* x) {
+  // Initial guesses of the band solves of a step.  With P_n, C_n the predictor- and
+  // corrector-stage solutions of step n, the guesses are
+  //   predictor of step n+1:  C_n + (P_n - C_{n-1})     corrector:  P_{n+1} + (C_n - P_n)
+  // (one stage per step: 2 P_n - P_{n-1}); each is off by O(tau^2) where the previous
+  // solution alone is off by O(tau).  Three full-grid slots hold the history; the solve
+  // writes its solution into the slot of the oldest entry.  Without history the guess is the
+  // previous solution (the band values of w_).
+  CGGuess<T> next_guess(bool corrector, bool rk2) {
+    CGGuess<T> gs{w_, nullptr, nullptr, (T)0, (T)0, nullptr};
+    int out = hO_;
+    if (out < 0)
+      for (int k = 0; k < 3; ++k)
+        if (k != hP_ && k != hC_) {
+          out = k;
+          break;
+        }
+    if (!corrector) {
+      if (rk2 && hC_ >= 0 && hP_ >= 0 && hO_ >= 0) {
+        gs = {hs_[hC_], hs_[hP_], hs_[hO_], (T)1, (T)-1, nullptr};
+      } else if (!rk2 && hP_ >= 0 && hO_ >= 0) {
+        gs = {hs_[hP_], hs_[hP_], hs_[hO_], (T)1, (T)-1, nullptr};
+      } else if (rk2 && hC_ >= 0) {
+        gs.a = hs_[hC_];
+      } else if (hP_ >= 0) {
+        gs.a = hs_[hP_];
+      }
+      hO_ = hP_;
+      hP_ = out;
+    } else {
+      if (hO_ >= 0 && hC_ >= 0) gs = {hs_[hP_], hs_[hC_], hs_[hO_], (T)1, (T)-1, nullptr};
+      else if (hP_ >= 0) gs.a = hs_[hP_];
+      hO_ = hC_;
+      hC_ = out;
+    }
+    gs.hist = hs_[out];
+    return gs;
+  }
+
+  template <typename Rhs> void cg_solve(Rhs rhs, T* x, CGGuess<T> gs = CGGuess<T>{}) {
+    if (!gs.a) gs.a = x;
     CGVec<T> v = cg_;
     CGCtl c;
     c.acc = acc_;
@@ -531,7 +574,7 @@ template <typename T> class Stepper : public PlanBase {
     const int* cnt = count_;
     T* wfull = x;
     MGP<T> mg = mgp();
-    void* args[] = {&idx, &cnt, &v, &wfull, &rhs, &c, &mg};
+    void* args[] = {&idx, &cnt, &v, &wfull, &rhs, &c, &mg, &gs};
     timed(ETD_K_CG, 0.0, [&] { ETD_CUDA(cudaLaunchCooperativeKernel((const void*)k, grid, 1024, args, 0, st_)); });
   }
 
@@ -688,6 +731,7 @@ template <typename T> class Stepper : public PlanBase {
     compute_band(phi);
     if (w_reset_) {
       ETD_CUDA(cudaMemsetAsync(w_, 0, sizeof(T) * g_.n, st_));
+      hP_ = hC_ = hO_ = -1;
       w_reset_ = false;
     } else {
       k_zero_left<<<nsm_ * 4, 256, 0, st_>>>(idx_old_, count_old_, mask_, (void*)w_, (int)sizeof(T));
@@ -737,7 +781,7 @@ template <typename T> class Stepper : public PlanBase {
       launch_reduce(1, u, G_, scal_ + S_MASS);
       // u-stage: new g times old u (Sec. 3.3)
       band_for_solve(nxt, G_);
-      cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_);
+      cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_, next_guess(false, rk2));
       timed(ETD_K_POINTWISE, 2 * fld(), [&] {
         k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, nxt, cur, u, w_, scal_, hvol_, r2_);
       });
@@ -746,10 +790,10 @@ template <typename T> class Stepper : public PlanBase {
       OpUPred<T> upred{1, sSu_, rk2 ? 1 : 0, sk_};
       passb(upred, I_[0], I_[1], outs({I_[0]}));
       if (rk2) {
-        inv(I_[0], EpiRecover<T>{ut_, G_, mc_.delta});
+        inv(I_[0], EpiRecover<T>{ut_, G_, u, mc_.delta});
         ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
         launch_reduce(1, ut_, G_, scal_ + S_MASS);
-        cg_solve(RhsGU<T>{G_, ut_, P_.ubar}, w_);
+        cg_solve(RhsGU<T>{G_, ut_, P_.ubar}, w_, next_guess(true, rk2));
         timed(ETD_K_POINTWISE, 2 * fld(), [&] {
           k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, nxt, cur, ut_, w_, scal_, hvol_, r2_);
         });
@@ -757,7 +801,7 @@ template <typename T> class Stepper : public PlanBase {
         OpUCorr<T> ucorr{1, sSu_, sk_};
         passb(ucorr, I_[0], nullptr, outs({I_[0]}));
       }
-      inv(I_[0], EpiRecover<T>{u, G_, mc_.delta});
+      inv(I_[0], EpiRecover<T>{u, G_, u, mc_.delta});
       std::swap(cur, nxt);
     }
     ETD_CUDA(cudaMemcpyAsync(phi, cur, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
@@ -781,23 +825,23 @@ template <typename T> class Stepper : public PlanBase {
     for (int n = 0; n < nsteps; ++n) {
       ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
       launch_reduce(2, u, G_, scal_ + S_MASS);
-      cg_solve(RhsGF<T>{G_, u}, w_);
+      cg_solve(RhsGF<T>{G_, u}, w_, next_guess(false, rk2));
       k_r2_fixed<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, G_, mask_, u, w_, scal_, hvol_, r2_);
       fwd(ProMul<T>{G_, u}, I_[0]);
       fwd(ProLoad<T>{r2_}, I_[1]);
       OpUPred<T> upred{1, sSu_, rk2 ? 1 : 0, sk_};
       passb(upred, I_[0], I_[1], outs({I_[0]}));
       if (rk2) {
-        inv(I_[0], EpiRecover<T>{ut_, G_, mc_.delta});
+        inv(I_[0], EpiRecover<T>{ut_, G_, u, mc_.delta});
         ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
         launch_reduce(2, ut_, G_, scal_ + S_MASS);
-        cg_solve(RhsGF<T>{G_, ut_}, w_);
+        cg_solve(RhsGF<T>{G_, ut_}, w_, next_guess(true, rk2));
         k_r2_fixed<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, G_, mask_, ut_, w_, scal_, hvol_, r2_);
         fwd(ProLoad<T>{r2_}, I_[0]);
         OpUCorr<T> ucorr{1, sSu_, sk_};
         passb(ucorr, I_[0], nullptr, outs({I_[0]}));
       }
-      inv(I_[0], EpiRecover<T>{u, G_, mc_.delta});
+      inv(I_[0], EpiRecover<T>{u, G_, u, mc_.delta});
     }
     ETD_CUDA(cudaGetLastError());
   }
@@ -910,6 +954,8 @@ template <typename T> class Stepper : public PlanBase {
   unsigned* bar_ = nullptr;
   int *status_ = nullptr, *flag_ = nullptr, *cg_iters_ = nullptr;
   bool a0_set_ = false, fixed_ready_ = false, band_dirty_ = false, w_reset_ = true;
+  T* hs_[3] = {};                 // solution history of the band solves (full grid)
+  int hP_ = -1, hC_ = -1, hO_ = -1;  // slots: last predictor, last corrector, the older entry
 };
 
 }  // namespace etd
