@@ -614,8 +614,10 @@ __device__ __forceinline__ bool grid_sync(const CGCtl& c) {
 // With piecewise-constant prolongation P the Galerkin operator P^T A P of a graph Laplacian
 // is again a graph Laplacian whose coupling between two neighbouring aggregates is the sum
 // of the fine couplings crossing between them, so every level keeps the 7-point compact
-// form (c, nb, inverse diagonal).  The preconditioner is one symmetric V(1,1) cycle with
-// weighted Jacobi (omega) and an even number of Jacobi sweeps on the coarsest level.
+// form (c, nb, inverse diagonal).  The preconditioner is one symmetric V(nu,nu) cycle whose
+// smoother is weighted Jacobi; with nu = 2 the two sweeps use the weight pair w1, w2 of the
+// degree-2 Chebyshev polynomial in D^-1 A (the two sweeps commute, so the cycle stays
+// symmetric), and the coarsest level takes an even number of sweeps with the same pair.
 constexpr int kMGMax = 7;
 
 template <typename T> struct MGL {
@@ -638,7 +640,7 @@ template <typename T> struct MGP {
   int gl;              // levels 0..gl-1 are processed by the whole grid, the rest by block 0
   int csweeps;         // Jacobi sweeps on the coarsest level (even)
   int nu;              // pre- and post-smoothing sweeps (1 or 2)
-  T omega;
+  T w1, w2;            // Jacobi weights of the first and second sweep (one Chebyshev pair)
   T alpha;             // over-correction of the coarse-grid correction
   MGL<T> L[kMGMax];
 };
@@ -758,7 +760,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
                          double* rr_out) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   PhaseSync ps{true, true};
-  const T om = mg.omega, al = mg.alpha;
+  const T w1 = mg.w1, w2 = mg.w2, al = mg.alpha;
   // after the barrier that follows the fused sweep: every block sees (r_new, r_new)
   auto fused_check = [&]() -> bool {
     const double rr = *(volatile double*)F.rr;
@@ -791,12 +793,12 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
           X[i] = __ldcg(X + i) + a * __ldcg(P + i);
           b0[i] = bi;
           rr += (double)bi * (double)bi;
-          const T ei = om * Lidg[i] * bi;
+          const T ei = w1 * Lidg[i] * bi;
           T s = 0;
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += Lc[f * cap + i] * (ei - om * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
+            s += Lc[f * cap + i] * (ei - w1 * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
           }
           Le[i] = ei;
           r1out[i] = bi - s;
@@ -807,12 +809,12 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll 2
         for (int i = t0; i < M; i += ns) {
           const T bi = __ldcg(Lb + i);
-          const T ei = om * Lidg[i] * bi;
+          const T ei = w1 * Lidg[i] * bi;
           T s = 0;
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += Lc[f * cap + i] * (ei - om * Lidg[j] * __ldcg(Lb + j));
+            s += Lc[f * cap + i] * (ei - w1 * Lidg[j] * __ldcg(Lb + j));
           }
           Le[i] = ei;
           r1out[i] = bi - s;
@@ -847,8 +849,8 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
             const int j = Lnb[f * cap + i];
             s += Lc[f * cap + i] * (di - Lidg[j] * __ldcg(Lo + j));
           }
-          Le[i] = __ldcg(Le + i) + om * di;
-          atomicAdd(Cb + Lagg[i], oi - om * s);
+          Le[i] = __ldcg(Le + i) + w2 * di;
+          atomicAdd(Cb + Lagg[i], oi - w2 * s);
         }
       }
       continue;
@@ -878,7 +880,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
     if (!ps.step(grid, c)) return -1;
     if (grid || blockIdx.x == 0) {
       const int M = *L.cnt;
-      for (int i = t0; i < M; i += ns) L.e[i] = om * L.idg[i] * __ldcg(L.b + i);
+      for (int i = t0; i < M; i += ns) L.e[i] = w1 * L.idg[i] * __ldcg(L.b + i);
     }
     for (int s = 1; s < mg.csweeps; ++s) {
       if (!ps.step(grid, c)) return -1;
@@ -886,7 +888,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
       T* dst = (s & 1) ? L.o : L.e;
       if (grid || blockIdx.x == 0) {
         const int M = *L.cnt;
-        for (int i = t0; i < M; i += ns) dst[i] = __ldcg(src + i) + om * L.idg[i] * (__ldcg(L.b + i) - mg_apply(L, src, i));
+        for (int i = t0; i < M; i += ns) dst[i] = __ldcg(src + i) + ((s & 1) ? w2 : w1) * L.idg[i] * (__ldcg(L.b + i) - mg_apply(L, src, i));
       }
     }
   }
@@ -917,7 +919,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
           s += Lc[f * cap + i] * (ei - (__ldcg(Le + j) + al * __ldcg(Co + Lagg[j])));
         }
         const T bi = __ldcg(Lb + i);
-        const T o1 = ei + om * Lidg[i] * (bi - s);
+        const T o1 = ei + (mg.nu == 2 ? w2 : w1) * Lidg[i] * (bi - s);
         out[i] = o1;
         if (l == 0 && mg.nu == 1) acc += (double)bi * (double)o1;
       }
@@ -939,7 +941,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll
           for (int f = 0; f < 6; ++f) s += Lc[f * cap + i] * (ti - __ldcg(Lt + Lnb[f * cap + i]));
           const T bi = __ldcg(Lb + i);
-          const T o2 = ti + om * Lidg[i] * (bi - s);
+          const T o2 = ti + w1 * Lidg[i] * (bi - s);
           Lo[i] = o2;
           if (l == 0) acc += (double)bi * (double)o2;
         }

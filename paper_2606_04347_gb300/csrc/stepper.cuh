@@ -580,9 +580,9 @@ template <typename T> class Stepper : public PlanBase {
 
   // Level l coarsens the grid 2x per axis l times (z only in 3D) while every coarsened
   // extent stays >= 4; levels whose full grid has >= 2^15 cells run on the whole GPU in the
-  // V-cycle, smaller ones on one block.  The cycle is V(2,2) with Jacobi (omega = 2/3), the
-  // coarse-grid correction over-corrected by 1.9 (piecewise-constant aggregation
-  // under-estimates it) and 2 Jacobi sweeps on the coarsest level.
+  // V-cycle, smaller ones on one block.  The cycle is V(2,2) with a degree-2 Chebyshev pair of
+  // Jacobi weights, the coarse-grid correction over-corrected by 1.9 (piecewise-constant
+  // aggregation under-estimates it) and 2 sweeps on the coarsest level.
   void init_multigrid() {
     int lz = 0;
     while ((1 << lz) < g_.nz) ++lz;
@@ -660,7 +660,14 @@ template <typename T> class Stepper : public PlanBase {
     m.gl = mg_gl_;
     m.csweeps = 2;
     m.nu = 2;
-    m.omega = (T)(2.0 / 3.0);
+    // degree-2 Chebyshev weights for D^-1 A on [lmax / 4, lmax], lmax = 2 (Gershgorin bound
+    // for the Jacobi-scaled graph Laplacian): w_i = 1 / (c + r cos((2 i + 1) pi / 4))
+    {
+      const double lmax = 2.0, lmin = lmax / 4.0, cth = 0.5 * (lmax + lmin), rad = 0.5 * (lmax - lmin);
+      const double cq = std::sqrt(0.5);
+      m.w1 = (T)(1.0 / (cth + rad * cq));
+      m.w2 = (T)(1.0 / (cth - rad * cq));
+    }
     m.alpha = (T)1.9;
     for (int l = 0; l < mg_nlev_; ++l) {
       const HostLevel& H = lv_[l];
