@@ -73,8 +73,22 @@ struct Geo {
 // Shared-memory padding: one spare slot every 16 complex elements (bank spreading).
 __host__ __device__ __forceinline__ int pad16(int k) { return k + (k >> 4); }
 
-// Lanes per team for a transform of length L (R = L / S values per lane).
-__host__ __device__ __forceinline__ int team_lanes(int L) { return L >= 64 ? 32 : (L >= 2 ? L / 2 : 1); }
+// R and S of the team transform of an axis of length n (a power of two up to 256): S lanes
+// with R = min(n, 16) values each.
+__host__ __device__ __forceinline__ constexpr int team_R(int n) { return n < 16 ? n : 16; }
+__host__ __device__ __forceinline__ constexpr int team_S(int n) { return n / team_R(n); }
+
+// Tile row pitches.  A team's exchange scratch (S (R + 1) values) lives in the rows it works
+// on: a pair of pass-A rows, one pass-B row.
+__host__ __device__ __forceinline__ int pitch_a(int nx) {
+  const int p = pad16(nx / 2) + 1, need = (team_S(nx) * (team_R(nx) + 1) + 1) / 2;
+  return p > need ? p : need;
+}
+__host__ __device__ __forceinline__ int pitch_b(int nz) {
+  const int p = pad16(nz - 1) + 1, need = team_S(nz) * (team_R(nz) + 1);
+  return p > need ? p : need;
+}
+
 
 // Tile choice shared by the plan and the allocation-free entry point.  Returns false if the
 // grid is not supported.  smemA: pass-A tile; smemB1: one pass-B operand tile.
@@ -84,7 +98,7 @@ inline bool choose_tiles(Geo& g, size_t csize, size_t& smemA, size_t& smemB1) {
   if (g.Y1 > 16 || g.Y2 < 2) return false;
   const int zb = csize == 8 ? ETD_ZB32 : (ETD_ZB32 > 1 ? ETD_ZB32 / 2 : 1);
   g.ZB = g.nz == 1 ? 1 : (g.nz < zb ? g.nz : zb);
-  const int rsa = pad16(g.nxh - 1) + 1;
+  const int rsa = pitch_a(g.nx);
   smemA = (size_t)g.ZB * g.Y2 * rsa * csize;
   if (g.nz > 1) {
     g.KB = 1;
@@ -92,7 +106,7 @@ inline bool choose_tiles(Geo& g, size_t csize, size_t& smemA, size_t& smemB1) {
     g.KB = 512 / g.Y1;
     if (g.KB > g.nxh) g.KB = g.nxh;
   }
-  const int rsb = pad16(g.nz - 1) + 1;
+  const int rsb = pitch_b(g.nz);
   smemB1 = (size_t)g.KB * g.Y1 * rsb * csize;
   return smemA <= 200 * 1024 && 2 * smemB1 <= 200 * 1024;
 }
@@ -183,44 +197,46 @@ template <typename C, int N, bool INV> __device__ __forceinline__ void dftN(C* v
   else if (N == 16) dft16<C, INV>(v);
 }
 
-template <typename C> __device__ __forceinline__ C shfl_xor_c(C v, int m) {
-  return C{__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
-}
 
-__device__ __forceinline__ int bitrev_bits(int t, int bits) { return bits ? (int)(__brev((unsigned)t) >> (32 - bits)) : 0; }
-
-// Team FFT of length L = R * S (S lanes, lane rank t; axes up to 256 points use R <= 8).  Forward: v[j] = x[t + S j] in,
-// v[k1] = X[k1 + R bitrev(t)] out.  Inverse: the reverse layouts, unnormalised.  Every
-// lane of the warp must call it (shuffles use the full mask).
-template <typename C, int R, bool INV>
-__device__ __forceinline__ void team_fft(C (&v)[R], int t, int S, const C* __restrict__ tw) {
-  const int L = R * S;
-  if (!INV) {
-    dftN<C, R, false>(v);
+// Team FFT of length N = R * S on S lanes (lane rank t) holding R values each, R = min(N, 16).
+// Lane t holds element t + S r in v[r] on entry and on exit, in both directions.  Forward:
+// an R-point DFT over r in registers, the twiddle w_N^(t k1), one exchange through the team's
+// shared-memory scratch (pitch R + 1: conflict-free both ways), then R/S DFTs of length S
+// over the former lane index; element k1 + R k2 with k1 = t + S h lands in v[h + (R/S) k2].
+// The inverse (unnormalised) is the forward transform of the conjugate, conjugated.  scr
+// holds S (R + 1) values and may alias the data the lanes just loaded (the call starts with a
+// warp barrier); every lane of the warp must call it, and teams without work pass act = false
+// (they keep off the scratch but still take the warp barriers).
+template <typename C, int R, int S, bool INV>
+__device__ __forceinline__ void team_fft(C (&v)[R], int t, C* scr, const C* __restrict__ tw, bool act = true) {
+  if (INV) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+  }
+  dftN<C, R, false>(v);
+  if (S > 1) {
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[t * k1]));
-    for (int h = S >> 1; h >= 1; h >>= 1) {
-      const C w = __ldg(&tw[(t & (h - 1)) * (L / (2 * h))]);
-      const bool up = (t & h) != 0;
+    __syncwarp();
+    if (act) {
 #pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) {
-        const C p = shfl_xor_c(v[k1], h);
-        v[k1] = up ? cmul(csub(p, v[k1]), w) : cadd(v[k1], p);
-      }
+      for (int k1 = 0; k1 < R; ++k1) scr[t * (R + 1) + k1] = v[k1];
     }
-  } else {
-    for (int h = 1; h < S; h <<= 1) {
-      const C w = __ldg(&tw[(t & (h - 1)) * (L / (2 * h))]);
-      const bool up = (t & h) != 0;
+    __syncwarp();
+    constexpr int H = R / S;
 #pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) {
-        const C p = shfl_xor_c(v[k1], h);
-        v[k1] = up ? csub(p, cmulc(v[k1], w)) : cadd(v[k1], cmulc(p, w));
-      }
+    for (int h = 0; h < H; ++h) {
+      C u[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) u[q] = act ? scr[q * (R + 1) + t + S * h] : C{0, 0};
+      dftN<C, S, false>(u);
+#pragma unroll
+      for (int k2 = 0; k2 < S; ++k2) v[h + H * k2] = u[k2];
     }
+  }
+  if (INV) {
 #pragma unroll
-    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmulc(v[k1], __ldg(&tw[t * k1]));
-    dftN<C, R, true>(v);
+    for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
   }
 }
 
@@ -259,16 +275,14 @@ template <typename C> struct OutP {
 // ---- pass A: x real-to-complex + inner y DFT ------------------------------------------
 // Tile: rows r = zz * Y2 + j (plane z0 + zz, y = n1 + Y1 j), row stride pad16(nxh-1)+1.
 
-template <typename T, typename Pro, int R>
+template <typename T, typename Pro, int R, int S>
 __device__ __forceinline__ void passA_rows_fwd(const Geo& g, const Pro& pro, typename Cplx<T>::type* tile, int rs,
                                                int z0, int n1, const typename Cplx<T>::type* __restrict__ twx) {
   using C = typename Cplx<T>::type;
-  const int S = g.nx / R, lS = __ffs(S) - 1;
-  const int lane = threadIdx.x & 31, t = lane & (S - 1);
+  const int t = threadIdx.x & (S - 1);
   const int team = threadIdx.x / S, nteams = blockDim.x / S;
   const int ncrows = (g.ZB * g.Y2) >> 1;
-  const int N = g.nx, half = g.nx >> 1;
-  constexpr int MU = R / 2 + 1;
+  const int half = g.nx >> 1;
   for (int base = 0; base < ncrows; base += nteams) {
     const int q = base + team;
     const bool ok = q < ncrows;
@@ -281,33 +295,29 @@ __device__ __forceinline__ void passA_rows_fwd(const Geo& g, const Pro& pro, typ
       const int x = t + S * j;
       v[j] = ok ? C{pro(i0 + x), pro(i1 + x)} : C{0, 0};
     }
-    team_fft<C, R, false>(v, t, S, twx);
-    C* row = tile + r0 * rs;
-    if (ok) {
-      const int br = bitrev_bits(t, lS);
-#pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) row[pad16(k1 + R * br)] = v[k1];
-    }
+    // the row pair's two tile rows (2 rs >= S (R + 1) values) double as the exchange scratch
+    C* row = tile + (ok ? r0 : 0) * rs;
+    team_fft<C, R, S, false>(v, t, row, twx, ok);
     __syncwarp();
-    // unpack the two real rows: A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i)
-    C a[MU], b[MU];
+    // unpack the two real rows, A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i),
+    // for k = t + S r <= N/2.  Z[N-k] sits on lane (S - t) mod S in register R-1-r (R-r mod R
+    // on lane 0), fetched with one shuffle per value.
+    const int pl = (S - t) & (S - 1);
 #pragma unroll
-    for (int m = 0; m < MU; ++m) {
-      const int k = t + S * m;
-      if (ok && k <= half) {
-        a[m] = row[pad16(k)];
-        b[m] = row[pad16((N - k) & (N - 1))];
+    for (int r = 0; r <= R / 2; ++r) {
+      const C send = (t == 0) ? v[(R - r) % R] : v[R - 1 - r];
+      C zc;
+      if (S > 1) {
+        zc.x = __shfl_sync(0xffffffffu, send.x, pl, S);
+        zc.y = __shfl_sync(0xffffffffu, send.y, pl, S);
+      } else {
+        zc = send;
       }
-    }
-    __syncwarp();
-    if (ok) {
-#pragma unroll
-      for (int m = 0; m < MU; ++m) {
-        const int k = t + S * m;
-        if (k <= half) {
-          row[pad16(k)] = C{(T)0.5 * (a[m].x + b[m].x), (T)0.5 * (a[m].y - b[m].y)};
-          row[rs + pad16(k)] = C{(T)0.5 * (a[m].y + b[m].y), (T)0.5 * (b[m].x - a[m].x)};
-        }
+      const int k = t + S * r;
+      if (ok && k <= half) {
+        const C z = v[r];
+        row[pad16(k)] = C{(T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y)};
+        row[rs + pad16(k)] = C{(T)0.5 * (z.y + zc.y), (T)0.5 * (zc.x - z.x)};
       }
     }
     __syncwarp();
@@ -342,13 +352,16 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);
-  const int rs = pad16(g.nxh - 1) + 1;
+  const int rs = pitch_a(g.nx);
   const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
   const int z0 = zb * g.ZB;
-  switch (g.nx / team_lanes(g.nx)) {
-    case 2: passA_rows_fwd<T, Pro, 2>(g, pro, tile, rs, z0, n1, twx); break;
-    case 4: passA_rows_fwd<T, Pro, 4>(g, pro, tile, rs, z0, n1, twx); break;
-    default: passA_rows_fwd<T, Pro, 8>(g, pro, tile, rs, z0, n1, twx); break;
+  switch (g.nx) {
+    case 8: passA_rows_fwd<T, Pro, 8, 1>(g, pro, tile, rs, z0, n1, twx); break;
+    case 16: passA_rows_fwd<T, Pro, 16, 1>(g, pro, tile, rs, z0, n1, twx); break;
+    case 32: passA_rows_fwd<T, Pro, 16, 2>(g, pro, tile, rs, z0, n1, twx); break;
+    case 64: passA_rows_fwd<T, Pro, 16, 4>(g, pro, tile, rs, z0, n1, twx); break;
+    case 128: passA_rows_fwd<T, Pro, 16, 8>(g, pro, tile, rs, z0, n1, twx); break;
+    default: passA_rows_fwd<T, Pro, 16, 16>(g, pro, tile, rs, z0, n1, twx); break;
   }
   __syncthreads();
   switch (g.Y2) {
@@ -380,27 +393,24 @@ __device__ __forceinline__ void passA_cols_inv(const Geo& g, typename Cplx<T>::t
   }
 }
 
-template <typename T, typename Epi, int R>
-__device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, const typename Cplx<T>::type* tile,
-                                               int rs, int z0, int n1,
-                                               const typename Cplx<T>::type* __restrict__ twx) {
+template <typename T, typename Epi, int R, int S>
+__device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typename Cplx<T>::type* tile, int rs,
+                                               int z0, int n1, const typename Cplx<T>::type* __restrict__ twx) {
   using C = typename Cplx<T>::type;
-  const int S = g.nx / R, lS = __ffs(S) - 1;
-  const int lane = threadIdx.x & 31, t = lane & (S - 1);
+  const int t = threadIdx.x & (S - 1);
   const int team = threadIdx.x / S, nteams = blockDim.x / S;
   const int ncrows = (g.ZB * g.Y2) >> 1;
   const int N = g.nx, half = g.nx >> 1;
-  const int br = bitrev_bits(t, lS);
   for (int base = 0; base < ncrows; base += nteams) {
     const int q = base + team;
     const bool ok = q < ncrows;
     const int r0 = 2 * q, r1 = r0 + 1;
-    const C* ra = tile + r0 * rs;
+    C* ra = tile + (ok ? r0 : 0) * rs;
     const C* rb = ra + rs;
     C v[R];
 #pragma unroll
-    for (int k1 = 0; k1 < R; ++k1) {
-      const int k = k1 + R * br;
+    for (int r = 0; r < R; ++r) {
+      const int k = t + S * r;
       C A = C{0, 0}, B = C{0, 0};
       if (ok) {
         if (k <= half) {
@@ -417,9 +427,10 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, con
           B.y = -B.y;
         }
       }
-      v[k1] = C{A.x - B.y, A.y + B.x};
+      v[r] = C{A.x - B.y, A.y + B.x};
     }
-    team_fft<C, R, true>(v, t, S, twx);
+    // the pair's rows, now held in registers, serve as the exchange scratch
+    team_fft<C, R, S, true>(v, t, ra, twx, ok);
     if (ok) {
       const long long i0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx;
       const long long i1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx;
@@ -440,7 +451,7 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);
-  const int rs = pad16(g.nxh - 1) + 1;
+  const int rs = pitch_a(g.nx);
   const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
   const int z0 = zb * g.ZB;
   switch (g.Y2) {
@@ -450,10 +461,13 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
     default: passA_cols_inv<T, 16>(g, tile, rs, z0, n1, in, twy); break;
   }
   __syncthreads();
-  switch (g.nx / team_lanes(g.nx)) {
-    case 2: passA_rows_inv<T, Epi, 2>(g, epi, tile, rs, z0, n1, twx); break;
-    case 4: passA_rows_inv<T, Epi, 4>(g, epi, tile, rs, z0, n1, twx); break;
-    default: passA_rows_inv<T, Epi, 8>(g, epi, tile, rs, z0, n1, twx); break;
+  switch (g.nx) {
+    case 8: passA_rows_inv<T, Epi, 8, 1>(g, epi, tile, rs, z0, n1, twx); break;
+    case 16: passA_rows_inv<T, Epi, 16, 1>(g, epi, tile, rs, z0, n1, twx); break;
+    case 32: passA_rows_inv<T, Epi, 16, 2>(g, epi, tile, rs, z0, n1, twx); break;
+    case 64: passA_rows_inv<T, Epi, 16, 4>(g, epi, tile, rs, z0, n1, twx); break;
+    case 128: passA_rows_inv<T, Epi, 16, 8>(g, epi, tile, rs, z0, n1, twx); break;
+    default: passA_rows_inv<T, Epi, 16, 16>(g, epi, tile, rs, z0, n1, twx); break;
   }
 }
 
@@ -500,41 +514,44 @@ __device__ __forceinline__ void passB_cols_any(const Geo& g, int kbn, const type
   }
 }
 
-template <typename T, typename Op, int R>
+template <typename T, typename Op, int R, int S>
 __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, int k2, int kbn, long long cb,
                                            typename Cplx<T>::type* tile0, typename Cplx<T>::type* tile1, int rs,
                                            OutP<typename Cplx<T>::type> outs,
                                            const typename Cplx<T>::type* __restrict__ twz) {
   using C = typename Cplx<T>::type;
-  const int S = g.nz / R, lS = __ffs(S) - 1;
-  const int lane = threadIdx.x & 31, t = lane & (S - 1);
+  // rows per team: one for z transforms of 8 points or more (16 rows of a 3D tile over at
+  // least 16 teams); two for the 2D tile (512 rows, 256 single-lane teams)
+  constexpr int RPT = R >= 8 ? 1 : 2;
+  const int t = threadIdx.x & (S - 1);
   const int team = threadIdx.x / S, nteams = blockDim.x / S;
   const int nrows = kbn * g.Y1;
-  const int br = bitrev_bits(t, lS);
-  // up to two rows per team, spectra kept in registers across the outputs
-  C base[2][R];
-  int rowid[2];
+  // spectra kept in registers across the outputs
+  C base[RPT][R];
+  int rowid[RPT];
 #pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
+  for (int rr = 0; rr < RPT; ++rr) {
     const int row = team + rr * nteams;
     rowid[rr] = row;
     const bool ok = row < nrows;
+    C* r0 = tile0 + (ok ? row : 0) * rs;
+    C* r1 = tile1 + (ok ? row : 0) * rs;
     C s0[R], s1[R];
     if (Op::NI >= 1) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) s0[j] = ok ? tile0[row * rs + pad16(t + S * j)] : C{0, 0};
-      team_fft<C, R, false>(s0, t, S, twz);
+      for (int j = 0; j < R; ++j) s0[j] = ok ? r0[pad16(t + S * j)] : C{0, 0};
+      team_fft<C, R, S, false>(s0, t, r0, twz, ok);
     }
     if (Op::NI >= 2) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) s1[j] = ok ? tile1[row * rs + pad16(t + S * j)] : C{0, 0};
-      team_fft<C, R, false>(s1, t, S, twz);
+      for (int j = 0; j < R; ++j) s1[j] = ok ? r1[pad16(t + S * j)] : C{0, 0};
+      team_fft<C, R, S, false>(s1, t, r1, twz, ok);
     }
     if (ok) {
       const int kxl = row / g.Y1, k1 = row - kxl * g.Y1;
 #pragma unroll
       for (int k = 0; k < R; ++k) {
-        const int kz = k + R * br;
+        const int kz = t + S * k;
         const Wave w = make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz);
         const int e = row * g.nz + kz;
         op.combine(e, cb + e, w, s0[k], s1[k]);
@@ -548,20 +565,22 @@ __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, 
   __syncthreads();
   for (int o = 0; o < op.nout; ++o) {
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
+    for (int rr = 0; rr < RPT; ++rr) {
       const int row = rowid[rr];
       const bool ok = row < nrows;
       C v[R];
       const int kxl = ok ? row / g.Y1 : 0, k1 = ok ? row - kxl * g.Y1 : 0;
 #pragma unroll
       for (int k = 0; k < R; ++k) {
-        const int kz = k + R * br;
+        const int kz = t + S * k;
         v[k] = ok ? op.out(o, base[rr][k], make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz)) : C{0, 0};
       }
-      team_fft<C, R, true>(v, t, S, twz);
+      C* r0 = tile0 + (ok ? row : 0) * rs;
+      team_fft<C, R, S, true>(v, t, r0, twz, ok);
+      __syncwarp();
       if (ok) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) tile0[row * rs + pad16(t + S * j)] = v[j];
+        for (int j = 0; j < R; ++j) r0[pad16(t + S * j)] = v[j];
       }
     }
     __syncthreads();
@@ -578,7 +597,7 @@ __global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_
                                              const typename Cplx<T>::type* __restrict__ twz) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int rs = pad16(g.nz - 1) + 1;
+  const int rs = pitch_b(g.nz);
   const int kb = blockIdx.x / g.Y2, k2 = blockIdx.x % g.Y2;
   const int kx0 = kb * g.KB;
   const int kbn = min(g.KB, g.nxh - kx0);
@@ -588,11 +607,14 @@ __global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_
   if (Op::NI >= 1) passB_cols_any<T, false>(g, kbn, in0, cb, tile0, rs, nullptr);
   if (Op::NI >= 2) passB_cols_any<T, false>(g, kbn, in1, cb, tile1, rs, nullptr);
   __syncthreads();
-  switch (g.nz / team_lanes(g.nz)) {
-    case 1: passB_rows<T, Op, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
-    case 2: passB_rows<T, Op, 2>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
-    case 4: passB_rows<T, Op, 4>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
-    default: passB_rows<T, Op, 8>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+  switch (g.nz) {
+    case 1: passB_rows<T, Op, 1, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 8: passB_rows<T, Op, 8, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 16: passB_rows<T, Op, 16, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 32: passB_rows<T, Op, 16, 2>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 64: passB_rows<T, Op, 16, 4>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    case 128: passB_rows<T, Op, 16, 8>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
+    default: passB_rows<T, Op, 16, 16>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
   }
 }
 
