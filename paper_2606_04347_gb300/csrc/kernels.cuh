@@ -323,17 +323,58 @@ template <typename T> __global__ void k_gloc(long long n, const T* __restrict__ 
 }
 
 // ---- FP64 reductions ---------------------------------------------------------------------
-// mode 0: sum a ; 1: sum G (u - ubar) ; 2: sum G (f(u) - ubar)
+// Per-thread compensated sum in the storage precision: hi collects the rounded partial sums,
+// lo the exact rounding error of each addition (Knuth's two-sum) plus any small parts the
+// caller adds.  In FP32 it carries about twice the working precision, so the FP64 sums of
+// the few per-thread partials match an FP64 accumulation while the per-element work stays
+// on the FP32 pipes (FP64 arithmetic is a small fraction of the FP32 rate on this part).
+template <typename T> struct CompSum {
+  T hi = 0, lo = 0;
+  __device__ __forceinline__ void add(T x) {
+    const T s = hi + x;
+    const T bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// mode 0: sum a ; 1: sum G (u - ubar) ; 2: sum G (f(u) - ubar).  FP64 storage sums in FP64;
+// FP32 storage forms each term to about twice FP32 precision (ubar split into hi + lo, the
+// product's rounding error from an FMA) and sums with CompSum.
 template <typename T>
 __global__ void k_reduce(long long n, int mode, const T* __restrict__ a, const T* __restrict__ G, double ubar,
                          double* dst) {
-  double s = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    if (mode == 0) s += (double)a[p];
-    else if (mode == 1) s += (double)G[p] * ((double)a[p] - ubar);
-    else s += (double)G[p] * ((double)find(a[p]) - ubar);
+  if constexpr (sizeof(T) == 8) {
+    double s = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+      if (mode == 0) s += (double)a[p];
+      else if (mode == 1) s += (double)G[p] * ((double)a[p] - ubar);
+      else s += (double)G[p] * ((double)find(a[p]) - ubar);
+    }
+    block_add(s, dst);
+    return;
   }
-  block_add(s, dst);
+  const float ub_hi = (float)ubar, ub_lo = (float)(ubar - (double)ub_hi);
+  CompSum<float> cs;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    if (mode == 0) {
+      cs.add((float)a[p]);
+      continue;
+    }
+    const float x = mode == 1 ? (float)a[p] : (float)find(a[p]);
+    const float g = (float)G[p];
+    // d = x - ubar as d_hi + d_lo (two-sum with the high part, then the low part)
+    const float dh = x - ub_hi;
+    const float bp = dh - x;
+    const float dl = ((x - (dh - bp)) + (-ub_hi - bp)) - ub_lo;
+    // g d = p + (error of the rounded product) + g d_lo
+    const float pr = g * dh;
+    const float pe = fmaf(g, dh, -pr);
+    cs.add(pr);
+    cs.lo += fmaf(g, dl, pe);
+  }
+  block_add(cs.value(), dst);
 }
 
 // Energy terms of Eq. (2.16) except the nonlocal one, plus the bound statistics and <phi,1>.
@@ -787,12 +828,12 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
         const T* __restrict__ P = F.p;
         T* __restrict__ X = F.x;
         const T a = F.a;
-        double rr = 0;
+        T rr = 0;  // per-thread partial in the storage precision (a few nodes per thread)
         for (int i = t0; i < M; i += ns) {
           const T bi = __ldcg(Ro + i) - a * __ldcg(Q + i);
           X[i] = __ldcg(X + i) + a * __ldcg(P + i);
           b0[i] = bi;
-          rr += (double)bi * (double)bi;
+          rr += bi * bi;
           const T ei = w1 * Lidg[i] * bi;
           T s = 0;
 #pragma unroll
@@ -803,7 +844,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
           Le[i] = ei;
           r1out[i] = bi - s;
         }
-        block_add(rr, F.rr);
+        block_add((double)rr, F.rr);
       } else {
         const T* __restrict__ Lb = l == 0 ? b0 : L.b;
 #pragma unroll 2
@@ -898,7 +939,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
     const bool grid = l < mg.gl;
     const int t0 = grid ? tid : threadIdx.x, ns = grid ? nth : blockDim.x;
     if (!ps.step(grid, c)) return -1;
-    double acc = 0;
+    T acc = 0;
     if (grid || blockIdx.x == 0) {
       T* __restrict__ out = mg.nu == 2 ? L.t : L.o;
       const T* __restrict__ Le = L.e;
@@ -921,7 +962,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
         const T bi = __ldcg(Lb + i);
         const T o1 = ei + (mg.nu == 2 ? w2 : w1) * Lidg[i] * (bi - s);
         out[i] = o1;
-        if (l == 0 && mg.nu == 1) acc += (double)bi * (double)o1;
+        if (l == 0 && mg.nu == 1) acc += bi * o1;
       }
     }
     if (mg.nu == 2) {
@@ -943,11 +984,11 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
           const T bi = __ldcg(Lb + i);
           const T o2 = ti + w1 * Lidg[i] * (bi - s);
           Lo[i] = o2;
-          if (l == 0) acc += (double)bi * (double)o2;
+          if (l == 0) acc += bi * o2;
         }
       }
     }
-    if (l == 0) block_add(acc, ru);
+    if (l == 0) block_add((double)acc, ru);
   }
   return 0;
 }
@@ -1100,7 +1141,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     const double gnew = *(volatile double*)(c.acc + A_RU + par);
     const double beta = gnew / gamma;
     const T bt = (T)beta;
-    double dun = 0;
+    T dun = 0;
     {
       const T* __restrict__ U = v.u;
       const T* __restrict__ Cc = v.c;
@@ -1116,10 +1157,10 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
         for (int f = 0; f < 6; ++f) w += Cc[f * cap + i] * (u - __ldcg(U + Nb[f * cap + i]));
         P[i] = u + bt * __ldcg(P + i);
         Q[i] = w + bt * __ldcg(Q + i);
-        dun += (double)w * (double)u;
+        dun += w * u;
       }
     }
-    block_add(dun, c.acc + A_DU + par);
+    block_add((double)dun, c.acc + A_DU + par);
     if (!grid_sync(c)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) c.acc[A_RU + par] = 0.0;
     delta = *(volatile double*)(c.acc + A_DU + par);
