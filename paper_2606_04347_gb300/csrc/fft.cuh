@@ -55,10 +55,10 @@ struct Geo {
 // Launch shapes of the pass kernels (threads per CTA, CTAs per SM the FP32 register budget
 // is sized for; FP64 kernels keep the full register file) and the number of z-planes per pass-A tile in FP32 (FP64 uses half).
 #ifndef ETD_PASSA_THREADS
-#define ETD_PASSA_THREADS 256
+#define ETD_PASSA_THREADS 512
 #endif
 #ifndef ETD_PASSA_MINB
-#define ETD_PASSA_MINB 4
+#define ETD_PASSA_MINB 2
 #endif
 #ifndef ETD_PASSB_THREADS
 #define ETD_PASSB_THREADS 256
@@ -67,7 +67,7 @@ struct Geo {
 #define ETD_PASSB_MINB 2
 #endif
 #ifndef ETD_ZB32
-#define ETD_ZB32 2
+#define ETD_ZB32 4
 #endif
 
 // Shared-memory padding: one spare slot every 16 complex elements (bank spreading).

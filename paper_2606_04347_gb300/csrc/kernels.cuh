@@ -141,6 +141,9 @@ template <typename T> struct EpiStore {
 // d = GU_new - G u_base, and on the recovery set {G > delta} u = GU_new / G is formed as
 // u_base + d / G (equal in exact arithmetic; the FP32 transform error then scales with the
 // increment instead of with G u itself), elsewhere u = GU_new = G u_base + d (Algorithm 1).
+__device__ __forceinline__ float div_inc(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_inc(double a, double b) { return a / b; }
+
 template <typename T> struct EpiRecover {
   T* out;
   const T* G;
@@ -149,16 +152,19 @@ template <typename T> struct EpiRecover {
   __device__ void operator()(long long i, T v) const {
     const T gg = G[i];
     const T ub = base[i];
-    out[i] = gg > delta ? ub + v / gg : gg * ub + v;
+    // the quotient only forms the increment d / G, so the 2-ulp fast division suffices in FP32
+    out[i] = gg > delta ? ub + div_inc(v, gg) : gg * ub + v;
   }
 };
 // phi^{n+1} and G^{n+1} = 18 (phi^2 - phi)^2 (Algorithm 1).
 template <typename T> struct EpiPhiG {
   T* phi;
   T* G;
+  T* zero;   // optional: a field cleared in the same pass (the band-list R2 fills its band later)
   __device__ void operator()(long long i, T v) const {
     phi[i] = v;
     G[i] = gloc(v);
+    if (zero) zero[i] = 0;
   }
 };
 
@@ -233,7 +239,39 @@ __device__ __forceinline__ void adv_flux(const Geo& g, const ModelC<T>& mc, cons
   Fz = s * pz;
 }
 
-// R2 of the coupled OK equation (Sec. 3.1) on the band of phin, 0 elsewhere.
+// R2 of the coupled OK equation (Sec. 3.1) at a band point p of phin.
+template <typename T>
+__device__ __forceinline__ T r2_coupled_at(const Geo& g, const ModelC<T>& mc, const T* __restrict__ phin,
+                                           const T* __restrict__ phio, const T* __restrict__ u,
+                                           const T* __restrict__ w, T mass, int p) {
+  const T f = phin[p];
+  const Nb n = neighbours(g, p);
+  const T gc = gloc(f);
+  const T gxm = gloc(phin[n.xm]), gxp = gloc(phin[n.xp]), gym = gloc(phin[n.ym]), gyp = gloc(phin[n.yp]);
+  const T gzm = g.nz > 1 ? gloc(phin[n.zm]) : (T)0, gzp = g.nz > 1 ? gloc(phin[n.zp]) : (T)0;
+  const T uc = u[p];
+  const T sl = surf_lap(g, mc, n, u, gc, gxm, gxp, gym, gyp, gzm, gzp);
+  const T guc = gc * uc;
+  T lapgu = (gxp * u[n.xp] - (T)2 * guc + gxm * u[n.xm]) * mc.ih2[0] +
+            (gyp * u[n.yp] - (T)2 * guc + gym * u[n.ym]) * mc.ih2[1];
+  if (g.nz > 1) lapgu += (gzp * u[n.zp] - (T)2 * guc + gzm * u[n.zm]) * mc.ih2[2];
+  T ax, ay, az, bx, by, bz;
+  adv_flux(g, mc, phin, phio, u, n.xp, ax, ay, az);
+  adv_flux(g, mc, phin, phio, u, n.xm, bx, by, bz);
+  T div = (ax - bx) * mc.i2h[0];
+  adv_flux(g, mc, phin, phio, u, n.yp, ax, ay, az);
+  adv_flux(g, mc, phin, phio, u, n.ym, bx, by, bz);
+  div += (ay - by) * mc.i2h[1];
+  if (g.nz > 1) {
+    adv_flux(g, mc, phin, phio, u, n.zp, ax, ay, az);
+    adv_flux(g, mc, phin, phio, u, n.zm, bx, by, bz);
+    div += (az - bz) * mc.i2h[2];
+  }
+  return mc.eps_u * (sl - mc.B1 * lapgu) + mc.B2 * guc - gc * dW(uc) / mc.eps_u - mc.gamma * gc * w[p] -
+         mc.M * gc * mass - div;
+}
+
+// R2 on the band of phin over the whole grid, 0 elsewhere (operator entry point).
 template <typename T>
 __global__ void k_r2_coupled(Geo g, ModelC<T> mc, const T* __restrict__ phin, const T* __restrict__ phio,
                              const T* __restrict__ u, const T* __restrict__ w, const double* __restrict__ scal,
@@ -241,34 +279,23 @@ __global__ void k_r2_coupled(Geo g, ModelC<T> mc, const T* __restrict__ phin, co
   const T mass = (T)(hvol * scal[S_MASS]);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
     const T f = phin[p];
-    if (mc.linear_only || !in_band(f, mc.band_hi)) {
-      out[p] = 0;
-      continue;
-    }
-    const Nb n = neighbours(g, p);
-    const T gc = gloc(f);
-    const T gxm = gloc(phin[n.xm]), gxp = gloc(phin[n.xp]), gym = gloc(phin[n.ym]), gyp = gloc(phin[n.yp]);
-    const T gzm = g.nz > 1 ? gloc(phin[n.zm]) : (T)0, gzp = g.nz > 1 ? gloc(phin[n.zp]) : (T)0;
-    const T uc = u[p];
-    const T sl = surf_lap(g, mc, n, u, gc, gxm, gxp, gym, gyp, gzm, gzp);
-    const T guc = gc * uc;
-    T lapgu = (gxp * u[n.xp] - (T)2 * guc + gxm * u[n.xm]) * mc.ih2[0] +
-              (gyp * u[n.yp] - (T)2 * guc + gym * u[n.ym]) * mc.ih2[1];
-    if (g.nz > 1) lapgu += (gzp * u[n.zp] - (T)2 * guc + gzm * u[n.zm]) * mc.ih2[2];
-    T ax, ay, az, bx, by, bz;
-    adv_flux(g, mc, phin, phio, u, n.xp, ax, ay, az);
-    adv_flux(g, mc, phin, phio, u, n.xm, bx, by, bz);
-    T div = (ax - bx) * mc.i2h[0];
-    adv_flux(g, mc, phin, phio, u, n.yp, ax, ay, az);
-    adv_flux(g, mc, phin, phio, u, n.ym, bx, by, bz);
-    div += (ay - by) * mc.i2h[1];
-    if (g.nz > 1) {
-      adv_flux(g, mc, phin, phio, u, n.zp, ax, ay, az);
-      adv_flux(g, mc, phin, phio, u, n.zm, bx, by, bz);
-      div += (az - bz) * mc.i2h[2];
-    }
-    out[p] = mc.eps_u * (sl - mc.B1 * lapgu) + mc.B2 * guc - gc * dW(uc) / mc.eps_u - mc.gamma * gc * w[p] -
-             mc.M * gc * mass - div;
+    out[p] = (mc.linear_only || !in_band(f, mc.band_hi)) ? (T)0 : r2_coupled_at(g, mc, phin, phio, u, w, mass, p);
+  }
+}
+
+// R2 at the points of the band list of phin only (the step: the rest of `out` was cleared
+// when phin was formed).  Consecutive threads take consecutive band points, so the stencil
+// work has no idle lanes.
+template <typename T>
+__global__ void k_r2_coupled_band(Geo g, ModelC<T> mc, const int* __restrict__ idx, const int* __restrict__ count,
+                                  const T* __restrict__ phin, const T* __restrict__ phio, const T* __restrict__ u,
+                                  const T* __restrict__ w, const double* __restrict__ scal, double hvol,
+                                  T* __restrict__ out) {
+  const T mass = (T)(hvol * scal[S_MASS]);
+  const int M = *count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int p = idx[i];
+    out[p] = mc.linear_only ? (T)0 : r2_coupled_at(g, mc, phin, phio, u, w, mass, p);
   }
 }
 

@@ -420,7 +420,7 @@ template <typename T> class Stepper : public PlanBase {
   static int pro_reads(const ProMul<T>&) { return 2; }
   static int epi_fields(const EpiStore<T>&) { return 1; }
   static int epi_fields(const EpiRecover<T>&) { return 3; }
-  static int epi_fields(const EpiPhiG<T>&) { return 2; }
+  static int epi_fields(const EpiPhiG<T>& e) { return e.zero ? 3 : 2; }
 
   template <typename Pro> void fwd(Pro pro, C* out) {
     auto k = passA_fwd<T, Pro>;
@@ -782,7 +782,7 @@ template <typename T> class Stepper : public PlanBase {
         OpPhiPred<T> pred{1, {0, 0, 0, 0, 0}, sphi_, sS_, 0, c_lap_, sk_};
         passb(pred, I_[0], I_[1], outs({I_[0]}));
       }
-      inv(I_[0], EpiPhiG<T>{nxt, G_});
+      inv(I_[0], EpiPhiG<T>{nxt, G_, r2_});
       ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double) * 2, st_));  // S_VOL, S_MASS
       launch_reduce(0, nxt, nullptr, scal_ + S_VOL);
       launch_reduce(1, u, G_, scal_ + S_MASS);
@@ -790,7 +790,7 @@ template <typename T> class Stepper : public PlanBase {
       band_for_solve(nxt, G_);
       cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_, next_guess(false, rk2));
       timed(ETD_K_POINTWISE, 2 * fld(), [&] {
-        k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, nxt, cur, u, w_, scal_, hvol_, r2_);
+        k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, u, w_, scal_, hvol_, r2_);
       });
       fwd(ProMul<T>{G_, u}, I_[0]);
       fwd(ProLoad<T>{r2_}, I_[1]);
@@ -802,7 +802,7 @@ template <typename T> class Stepper : public PlanBase {
         launch_reduce(1, ut_, G_, scal_ + S_MASS);
         cg_solve(RhsGU<T>{G_, ut_, P_.ubar}, w_, next_guess(true, rk2));
         timed(ETD_K_POINTWISE, 2 * fld(), [&] {
-          k_r2_coupled<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, nxt, cur, ut_, w_, scal_, hvol_, r2_);
+          k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, ut_, w_, scal_, hvol_, r2_);
         });
         fwd(ProLoad<T>{r2_}, I_[0]);
         OpUCorr<T> ucorr{1, sSu_, sk_};
