@@ -225,7 +225,10 @@ def run_ours(a):
     from paper_2606_04347_gb300 import workloads as wl
     prec = 1 if a.precision == "fp32" else 0
     p, phi0, u0, _ = wl.workload("c3", n=a.size, precision=prec)
-    p = p.replace(cg_rtol=1e-6 if prec else 1e-12)
+    # band-solve tolerance: FP64 solves to 1e-12; the FP32 form stops at 1e-5, where the
+    # FP32-vs-FP64 differences of phi, u and the energy after 20 steps at 256^3 are the same
+    # to three digits as with 1e-6 (they are set by FP32 rounding, not by the solve)
+    p = p.replace(cg_rtol=1e-5 if prec else 1e-12)
     dt_ = torch.float32 if prec else torch.float64
     stream = torch.cuda.current_stream()
     plan = Plan(p, stream=stream)
@@ -244,7 +247,6 @@ def run_ours(a):
     clk = Clocks(local)
     clk.start()
     time.sleep(0.3)
-    plan.timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     plan.step(phi, u, a.steps)
@@ -254,11 +256,20 @@ def run_ours(a):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clocks = clk.stop()
-    kt = plan.timing_read()
-    plan.timing(False)
     ms = allreduce_max(ms, world)
     value = aggregate(world, npts, a.steps, ms)
     d = plan.step(phi, u, 0, diag=True)
+    # a second run of the same number of steps with per-launch events (kernel classes,
+    # launch count and rooflines); the headline value above is timed without them
+    plan.timing(True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    plan.step(phi, u, a.steps)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = f0.elapsed_time(f1)
+    kt = plan.timing_read()
+    plan.timing(False)
 
     # dominant kernel class and its roofline
     dom = max(kt, key=lambda k: kt[k][0])
@@ -266,6 +277,9 @@ def run_ours(a):
     peak, peak_src = peaks()
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
     launches = int(sum(v[1] for v in kt.values()))
+    # whole step: every class's algorithmic bytes over the timed region's device time
+    step_bytes = sum(v[2] for v in kt.values())
+    step_achieved = step_bytes / (ms_t / 1e3) / 1e9
 
     # FP64 form of the same step on the same GPU (outside the timed region): speed-up of the
     # FP32-mixed form and agreement of the two after the same number of steps
@@ -350,8 +364,12 @@ def run_ours(a):
                          "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": recorded_traffic(dom, a.size, a.precision),
                          "algo_bytes_per_launch": dbytes / max(dn, 1), "avg_launch_ms": dms / max(dn, 1)},
+            "step_roofline": {"bound": "hbm", "bytes_per_step": step_bytes / a.steps,
+                              "bytes_per_point_step": step_bytes / a.steps / npts, "achieved": step_achieved,
+                              "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
             "fp64_gpu": fp64,
             "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
+            "kernel_ms_steps": a.steps, "timed_with_events_ms_per_step": ms_t / a.steps,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * npts * esize,
                     "d2h_bytes_per_step": 2 * npts * esize},
             "gpu_launches": launches,

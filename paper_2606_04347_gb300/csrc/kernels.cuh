@@ -290,9 +290,10 @@ template <typename T>
 __global__ void k_r2_coupled_band(Geo g, ModelC<T> mc, const int* __restrict__ idx, const int* __restrict__ count,
                                   const T* __restrict__ phin, const T* __restrict__ phio, const T* __restrict__ u,
                                   const T* __restrict__ w, const double* __restrict__ scal, double hvol,
-                                  T* __restrict__ out) {
+                                  T* __restrict__ out, unsigned long long* work) {
   const T mass = (T)(hvol * scal[S_MASS]);
   const int M = *count;
+  if (work && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(work, (unsigned long long)M);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
     const int p = idx[i];
     out[p] = mc.linear_only ? (T)0 : r2_coupled_at(g, mc, phin, phio, u, w, mass, p);
@@ -624,7 +625,7 @@ struct CGCtl {
   double rtol;
   int maxit;
   long long budget;     // clock cycles a barrier may wait
-  unsigned long long* work;  // accumulates band nodes x sweeps (measurement)
+  unsigned long long* work;  // accumulates band nodes x CG iterations (measurement)
 };
 
 // Inside the band CG kernel every vector that the kernel itself writes (x, r, u, p, q and
@@ -1213,7 +1214,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     *c.iters = k;
     *c.resid = bb > 0 ? sqrt(rr / bb) : 0.0;
     if (!conv) atomicCAS(c.status, 0, 5);
-    atomicAdd(c.work, (unsigned long long)(k + 3) * (unsigned long long)M);
+    atomicAdd(c.work, (unsigned long long)k * (unsigned long long)M);
   }
 }
 

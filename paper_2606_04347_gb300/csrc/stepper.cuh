@@ -323,8 +323,8 @@ template <typename T> class Stepper : public PlanBase {
     flag_ = alloc<int>(1);
     cg_iters_ = alloc<int>(1);
     cg_resid_ = alloc<double>(1);
-    cg_work_ = alloc<unsigned long long>(1);
-    ETD_CUDA(cudaMemset(cg_work_, 0, sizeof(unsigned long long)));
+    cg_work_ = alloc<unsigned long long>(2);
+    ETD_CUDA(cudaMemset(cg_work_, 0, 2 * sizeof(unsigned long long)));
     ETD_CUDA(cudaMemset(status_, 0, sizeof(int)));
     ETD_CUDA(cudaMemset(cg_iters_, 0, sizeof(int)));
     ETD_CUDA(cudaMemset(cg_resid_, 0, sizeof(double)));
@@ -789,8 +789,9 @@ template <typename T> class Stepper : public PlanBase {
       // u-stage: new g times old u (Sec. 3.3)
       band_for_solve(nxt, G_);
       cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_, next_guess(false, rk2));
-      timed(ETD_K_POINTWISE, 2 * fld(), [&] {
-        k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, u, w_, scal_, hvol_, r2_);
+      timed(ETD_K_POINTWISE, 0.0, [&] {  // bytes from the band-node counter
+        k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, u, w_, scal_, hvol_, r2_,
+                                                         cg_work_ + 1);
       });
       fwd(ProMul<T>{G_, u}, I_[0]);
       fwd(ProLoad<T>{r2_}, I_[1]);
@@ -801,8 +802,9 @@ template <typename T> class Stepper : public PlanBase {
         ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
         launch_reduce(1, ut_, G_, scal_ + S_MASS);
         cg_solve(RhsGU<T>{G_, ut_, P_.ubar}, w_, next_guess(true, rk2));
-        timed(ETD_K_POINTWISE, 2 * fld(), [&] {
-          k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, ut_, w_, scal_, hvol_, r2_);
+        timed(ETD_K_POINTWISE, 0.0, [&] {
+          k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, ut_, w_, scal_, hvol_, r2_,
+                                                           cg_work_ + 1);
         });
         fwd(ProLoad<T>{r2_}, I_[0]);
         OpUCorr<T> ucorr{1, sSu_, sk_};
@@ -869,7 +871,7 @@ template <typename T> class Stepper : public PlanBase {
         t_n_[k] = 0;
         t_timed_[k] = 0;
       }
-      ETD_CUDA(cudaMemset(cg_work_, 0, sizeof(unsigned long long)));
+      ETD_CUDA(cudaMemset(cg_work_, 0, 2 * sizeof(unsigned long long)));
     }
     timing_ = enable != 0;
   }
@@ -884,12 +886,18 @@ template <typename T> class Stepper : public PlanBase {
     }
     recs_.clear();
     unsigned long long work = 0;
-    ETD_CUDA(cudaMemcpy(&work, cg_work_, sizeof(work), cudaMemcpyDeviceToHost));
+    unsigned long long works[2] = {0, 0};
+    ETD_CUDA(cudaMemcpy(works, cg_work_, sizeof(works), cudaMemcpyDeviceToHost));
+    work = works[0];
     *ms = t_ms_[kind];
     *launches = t_n_[kind];
-    // band CG: 16 element accesses per band node and iteration (stencil on p; x, r, p, q,
-    // inverse diagonal and three face coefficients), counted from the device work counter
-    *bytes = kind == ETD_K_CG ? 16.0 * sizeof(T) * (double)work : t_bytes_[kind];
+    // band CG: 18 element accesses per band node and CG iteration (x, r, p, A p, three face
+    // coefficients and six neighbour indices, read or written: 72 B in FP32) times the
+    // measured iteration count, from the device work counter.  The multigrid V-cycle behind
+    // each iteration moves several times that; the count is the plain-CG figure on purpose.
+    *bytes = kind == ETD_K_CG ? 18.0 * sizeof(T) * (double)work : t_bytes_[kind];
+    // band-list R2: phi^n, phi^old, u, w read and R2 written once per band node
+    if (kind == ETD_K_POINTWISE) *bytes += 5.0 * sizeof(T) * (double)works[1];
   }
 
  private:
