@@ -170,30 +170,13 @@ template <typename T> struct EpiPhiG {
 
 // ---- pointwise / band kernels ----------------------------------------------------------
 
-// Lu = Delta_{S,h} u with g = g(phi), on the band of phi (0 elsewhere).
-template <typename T>
-__global__ void k_surf_lap_band(Geo g, ModelC<T> mc, const T* __restrict__ phi, const T* __restrict__ u,
-                                T* __restrict__ out) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (int)g.n; p += gridDim.x * blockDim.x) {
-    const T f = phi[p];
-    if (!in_band(f, mc.band_hi)) {
-      out[p] = 0;
-      continue;
-    }
-    const Nb n = neighbours(g, p);
-    const T gz_m = g.nz > 1 ? gloc(phi[n.zm]) : (T)0, gz_p = g.nz > 1 ? gloc(phi[n.zp]) : (T)0;
-    out[p] = surf_lap(g, mc, n, u, gloc(f), gloc(phi[n.xm]), gloc(phi[n.xp]), gloc(phi[n.ym]), gloc(phi[n.yp]),
-                      gz_m, gz_p);
-  }
-}
-
 // R1 without its Laplacian term (Sec. 3.1), and W'(phi) - A1 phi whose spectrum receives
 // kappa/(mu eps^2) lambda in pass B.  Delta phi and grad phi are spectral (pass-A outputs).
 template <typename T>
 __global__ void k_r1(Geo g, ModelC<T> mc, const T* __restrict__ phi, const T* __restrict__ lap,
                      const T* __restrict__ gx, const T* __restrict__ gy, const T* __restrict__ gz,
-                     const T* __restrict__ u, const T* __restrict__ lu, const double* __restrict__ scal,
-                     double hvol, T* __restrict__ out_rest, T* __restrict__ out_wm) {
+                     const T* __restrict__ u, const double* __restrict__ scal, double hvol,
+                     T* __restrict__ out_rest, T* __restrict__ out_wm) {
   const T e = mc.eps_phi, e2 = e * e;
   const T dvol = (T)(hvol * scal[S_VOL] - scal[S_A0]);
   const T c_a = mc.kappa / (mc.mu * e2);
@@ -212,8 +195,14 @@ __global__ void k_r1(Geo g, ModelC<T> mc, const T* __restrict__ phi, const T* __
     const T Wm = Wp - mc.A1 * f;
     const T uu = u[p];
     T r = c_a * (Wpp - mc.A2) * (L - mc.A1 * f / e2) - (c_b * Wpp + c_c) * Wm;
-    if (in_band(f, mc.band_hi))
-      r += (mc.lambda_line / mc.mu) * (mc.eps_u * lu[p] - gloc(f) * dW(uu) / mc.eps_u) * gn;
+    if (in_band(f, mc.band_hi)) {
+      // line-tension term with Delta_{S,h} u (g = g(phi) at the faces), band points only
+      const Nb n = neighbours(g, p);
+      const T gzm = g.nz > 1 ? gloc(phi[n.zm]) : (T)0, gzp = g.nz > 1 ? gloc(phi[n.zp]) : (T)0;
+      const T lu = surf_lap(g, mc, n, u, gloc(f), gloc(phi[n.xm]), gloc(phi[n.xp]), gloc(phi[n.ym]),
+                            gloc(phi[n.yp]), gzm, gzp);
+      r += (mc.lambda_line / mc.mu) * (mc.eps_u * lu - gloc(f) * dW(uu) / mc.eps_u) * gn;
+    }
     r += -(mc.M_area / mc.mu) * dvol * gn;
     r += (mc.alpha / mc.mu) * (uu + mc.u0) * gn * (e * L - Wp / e);
     out_rest[p] = r;
@@ -714,11 +703,13 @@ template <typename T> struct MGP {
   MGL<T> L[kMGMax];
 };
 
+// Multigrid set-up steps, written for any grid-stride partition (t0, ns) so that the large
+// levels run them as grid-wide kernels and the small ones all inside one block.
+
 // mark the cells of level l (grid lxc, lyc) holding nodes of level l-1 (grid lxf, lyf)
-static __global__ void k_mg_mark(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
-                                 int is3d, int lxc, int lyc, unsigned char* __restrict__ mark) {
-  const int M = *cnt;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void mg_mark_body(const int* __restrict__ list, int M, int lxf, int lyf, int is3d,
+                                             int lxc, int lyc, unsigned char* __restrict__ mark, int t0, int ns) {
+  for (int i = t0; i < M; i += ns) {
     const int p = list[i];
     const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
     const int C = (((is3d ? Z >> 1 : 0) << (lxc + lyc)) | ((Y >> 1) << lxc) | (X >> 1));
@@ -726,10 +717,10 @@ static __global__ void k_mg_mark(const int* __restrict__ list, const int* __rest
   }
 }
 
-static __global__ void k_mg_parent(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
-                                   int is3d, int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg) {
-  const int M = *cnt;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void mg_parent_body(const int* __restrict__ list, int M, int lxf, int lyf, int is3d,
+                                               int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg,
+                                               int t0, int ns) {
+  for (int i = t0; i < M; i += ns) {
     const int p = list[i];
     const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
     agg[i] = cmap[((is3d ? Z >> 1 : 0) << (lxc + lyc)) | ((Y >> 1) << lxc) | (X >> 1)];
@@ -738,14 +729,14 @@ static __global__ void k_mg_parent(const int* __restrict__ list, const int* __re
 
 // Galerkin couplings of level l from level l-1.
 template <typename T>
-__global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict__ ccnt, int lxc, int lyc, int lzc,
-                            int is3d, const unsigned char* __restrict__ fmark, const int* __restrict__ fmap,
-                            int lxf, int lyf, const T* __restrict__ fc, int fcap, const int* __restrict__ cmap,
-                            T* __restrict__ c, int* __restrict__ nb, T* __restrict__ idg, int* __restrict__ child,
-                            int cap) {
-  const int M = *ccnt;
+__device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, int M, int lxc, int lyc, int lzc,
+                                               int is3d, const unsigned char* __restrict__ fmark,
+                                               const int* __restrict__ fmap, int lxf, int lyf,
+                                               const T* __restrict__ fc, int fcap, const int* __restrict__ cmap,
+                                               T* __restrict__ c, int* __restrict__ nb, T* __restrict__ idg,
+                                               int* __restrict__ child, int cap, int t0, int ns) {
   const int mx = (1 << lxc) - 1, my = (1 << lyc) - 1, mz = (1 << lzc) - 1;
-  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < M; I += gridDim.x * blockDim.x) {
+  for (int I = t0; I < M; I += ns) {
     const int C = clist[I];
     const int X = C & mx, Y = (C >> lxc) & my, Z = C >> (lxc + lyc);
     T s[6] = {0, 0, 0, 0, 0, 0};
@@ -772,6 +763,90 @@ __global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict
       d += s[f];
     }
     idg[I] = d > (T)0 ? (T)1 / d : (T)1;
+  }
+}
+
+static __global__ void k_mg_mark(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
+                                 int is3d, int lxc, int lyc, unsigned char* __restrict__ mark) {
+  mg_mark_body(list, *cnt, lxf, lyf, is3d, lxc, lyc, mark, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
+}
+
+static __global__ void k_mg_parent(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
+                                   int is3d, int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg) {
+  mg_parent_body(list, *cnt, lxf, lyf, is3d, lxc, lyc, cmap, agg, blockIdx.x * blockDim.x + threadIdx.x,
+                 gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict__ ccnt, int lxc, int lyc, int lzc,
+                            int is3d, const unsigned char* __restrict__ fmark, const int* __restrict__ fmap,
+                            int lxf, int lyf, const T* __restrict__ fc, int fcap, const int* __restrict__ cmap,
+                            T* __restrict__ c, int* __restrict__ nb, T* __restrict__ idg, int* __restrict__ child,
+                            int cap) {
+  mg_coarse_body<T>(clist, *ccnt, lxc, lyc, lzc, is3d, fmark, fmap, lxf, lyf, fc, fcap, cmap, c, nb, idg, child, cap,
+                    blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// One level's arrays for the single-block set-up of the small levels.
+template <typename T> struct MGSetLevel {
+  int lx, ly, lz, cap;
+  int* cnt;
+  int* list;
+  int* map;
+  unsigned char* mark;
+  T* c;
+  int* nb;
+  T* idg;
+  int* agg;
+  int* child;
+};
+
+template <typename T> struct MGSetTail {
+  int first, nlev, is3d;
+  MGSetLevel<T> L[kMGMax];
+};
+
+// Levels first..nlev-1 built in order by one block of 1024 threads: mark, compact (one
+// contiguous chunk of cells per thread, block-wide exclusive scan), parent map of the
+// finer level, Galerkin couplings.  The finer level of `first` is complete on entry.
+template <typename T> __global__ void __launch_bounds__(1024) k_mg_setup_tail(MGSetTail<T> a) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int l = a.first; l < a.nlev; ++l) {
+    const MGSetLevel<T>& F = a.L[l - 1];
+    const MGSetLevel<T>& L = a.L[l];
+    for (int i = tid; i < L.cap; i += nt) L.mark[i] = 0;
+    __syncthreads();
+    const int MF = *F.cnt;
+    mg_mark_body(F.list, MF, F.lx, F.ly, a.is3d, L.lx, L.ly, L.mark, tid, nt);
+    __syncthreads();
+    const int per = (L.cap + nt - 1) / nt;
+    const int lo = min(L.cap, tid * per), hi = min(L.cap, lo + per);
+    int own = 0;
+    for (int i = lo; i < hi; ++i) own += L.mark[i];
+    part[tid] = own;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+      const int v = tid >= off ? part[tid - off] : 0;
+      __syncthreads();
+      part[tid] += v;
+      __syncthreads();
+    }
+    int pos = part[tid] - own;
+    for (int i = lo; i < hi; ++i)
+      if (L.mark[i]) {
+        L.list[pos] = i;
+        L.map[i] = pos;
+        ++pos;
+      }
+    if (tid == nt - 1) *L.cnt = part[tid];
+    __syncthreads();
+    const int M = part[nt - 1];
+    mg_parent_body(F.list, MF, F.lx, F.ly, a.is3d, L.lx, L.ly, L.map, F.agg, tid, nt);
+    mg_coarse_body<T>(L.list, M, L.lx, L.ly, L.lz, a.is3d, F.mark, F.map, F.lx, F.ly, F.c, F.cap, L.map, L.c, L.nb,
+                      L.idg, L.child, L.cap, tid, nt);
+    __syncthreads();
   }
 }
 

@@ -293,7 +293,7 @@ template <typename T> class Stepper : public PlanBase {
     sphi_ = alloc<C>(g_.nhat);
     sS_ = alloc<C>(g_.nhat);
     sSu_ = alloc<C>(g_.nhat);
-    T** reals[] = {&phiA_, &phiB_, &phit_, &lap_, &gx_, &gy_, &gz_, &lu_, &rr_, &wm_, &r2_, &ut_, &G_, &w_,
+    T** reals[] = {&phiA_, &phiB_, &phit_, &lap_, &gx_, &gy_, &gz_, &rr_, &wm_, &r2_, &ut_, &G_, &w_,
                    &cg_.x, &cg_.r, &cg_.r1, &cg_.u, &cg_.p, &cg_.q, &cg_.idg};
     for (T** r : reals) *r = alloc<T>(g_.n);
     for (T** r : reals) ETD_CUDA(cudaMemset(*r, 0, sizeof(T) * g_.n));
@@ -628,10 +628,13 @@ template <typename T> class Stepper : public PlanBase {
     while (mg_gl_ < mg_nlev_ && lv_[mg_gl_].cap >= (1 << 15)) ++mg_gl_;
   }
 
-  // Coarse levels for the current band (level 0 = idx_, count_, mask_, bmap_, cg_).
+  // Coarse levels for the current band (level 0 = idx_, count_, mask_, bmap_, cg_).  Levels
+  // whose full grid has more than 2^15 cells use grid-wide kernels; the rest are built by
+  // one single-block launch (they are too small to fill the GPU, and launch gaps dominate).
   void mg_setup() {
     const int is3d = g_.nz > 1;
-    for (int l = 1; l < mg_nlev_; ++l) {
+    int l = 1;
+    for (; l < mg_nlev_ && lv_[l].cap > (1 << 15); ++l) {
       HostLevel& L = lv_[l];
       const HostLevel& F = lv_[l - 1];
       const int* flist = l == 1 ? idx_ : F.list;
@@ -650,6 +653,42 @@ template <typename T> class Stepper : public PlanBase {
         k_mg_coarse<T><<<nsm_ * 4, 256, 0, st_>>>(L.list, L.cnt, L.lx, L.ly, L.lz, is3d, fmark, fmap, F.lx, F.ly, fc,
                                                   F.cap, L.map, L.c, L.nb, L.idg, L.child, L.cap);
       });
+      ETD_CUDA(cudaGetLastError());
+    }
+    if (l < mg_nlev_) {
+      MGSetTail<T> a{};
+      a.first = l;
+      a.nlev = mg_nlev_;
+      a.is3d = is3d;
+      for (int k = 0; k < mg_nlev_; ++k) {
+        const HostLevel& H = lv_[k];
+        MGSetLevel<T>& S = a.L[k];
+        S.lx = H.lx;
+        S.ly = H.ly;
+        S.lz = H.lz;
+        S.cap = H.cap;
+        S.agg = H.agg;
+        if (k == 0) {
+          S.cnt = count_;
+          S.list = idx_;
+          S.map = bmap_;
+          S.mark = mask_;
+          S.c = cg_.c;
+          S.nb = cg_.nb;
+          S.idg = cg_.idg;
+          S.child = nullptr;
+        } else {
+          S.cnt = H.cnt;
+          S.list = H.list;
+          S.map = H.map;
+          S.mark = H.mark;
+          S.c = H.c;
+          S.nb = H.nb;
+          S.idg = H.idg;
+          S.child = H.child;
+        }
+      }
+      timed(ETD_K_BAND, 0.0, [&] { k_mg_setup_tail<T><<<1, 1024, 0, st_>>>(a); });
       ETD_CUDA(cudaGetLastError());
     }
   }
@@ -725,11 +764,8 @@ template <typename T> class Stepper : public PlanBase {
 
   // R1 parts at (phi, u): rr_ = R1 without the Laplacian term, wm_ = W'(phi) - A1 phi.
   void phi_terms(const T* phi, const T* u) {
-    timed(ETD_K_POINTWISE, 2 * fld(), [&] {
-      k_surf_lap_band<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, phi, u, lu_);
-    });
-    timed(ETD_K_POINTWISE, (g_.nz > 1 ? 9 : 8) * fld(), [&] {
-      k_r1<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, phi, lap_, gx_, gy_, gz_, u, lu_, scal_, hvol_, rr_, wm_);
+    timed(ETD_K_POINTWISE, (g_.nz > 1 ? 8 : 7) * fld(), [&] {
+      k_r1<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, phi, lap_, gx_, gy_, gz_, u, scal_, hvol_, rr_, wm_);
     });
     ETD_CUDA(cudaGetLastError());
   }
@@ -946,7 +982,7 @@ template <typename T> class Stepper : public PlanBase {
   C* I_[5] = {};
   C *sphi_ = nullptr, *sS_ = nullptr, *sSu_ = nullptr;
   T *phiA_ = nullptr, *phiB_ = nullptr, *phit_ = nullptr, *lap_ = nullptr, *gx_ = nullptr, *gy_ = nullptr,
-    *gz_ = nullptr, *lu_ = nullptr, *rr_ = nullptr, *wm_ = nullptr, *r2_ = nullptr, *ut_ = nullptr, *G_ = nullptr,
+    *gz_ = nullptr, *rr_ = nullptr, *wm_ = nullptr, *r2_ = nullptr, *ut_ = nullptr, *G_ = nullptr,
     *w_ = nullptr;
   CGVec<T> cg_{};
   unsigned char* mask_ = nullptr;
