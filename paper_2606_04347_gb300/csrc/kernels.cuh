@@ -1,6 +1,7 @@
 // kernels.cuh -- pointwise terms, finite-difference band terms, band compaction, the band
 // conjugate-gradient solve and FP64 reductions of the ETD membrane step.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include "fft.cuh"
 
@@ -534,6 +535,7 @@ template <typename T> struct CGVec {
   T* r1;                  // second residual buffer (the multigrid iterations alternate r, r1)
   T* idg;                 // inverse diagonal
   T* c;                   // face coefficients, c[d * cap + i], d = x+, x-, y+, y-, z+, z-
+  __half* c16;            // the same in FP16 for the multigrid sweeps (FP32 storage only, else null)
   int* nb;                // compact index of the face neighbour (i itself when absent)
   int cap;
 };
@@ -559,6 +561,7 @@ __global__ void k_cg_setup(Geo g, ModelC<T> mc, const int* __restrict__ idx, con
         j = bmap[q[f]];
       }
       v.c[f * v.cap + i] = c;
+      if (v.c16) v.c16[f * v.cap + i] = __float2half_rn((float)c);
       v.nb[f * v.cap + i] = j;
       d += c;
     }
@@ -700,6 +703,7 @@ template <typename T> struct MGP {
   int nu;              // pre- and post-smoothing sweeps (1 or 2)
   T w1, w2;            // Jacobi weights of the first and second sweep (one Chebyshev pair)
   T alpha;             // over-correction of the coarse-grid correction
+  const __half* c16;   // level-0 couplings in FP16 for the sweeps (null: use L[0].c)
   MGL<T> L[kMGMax];
 };
 
@@ -876,6 +880,13 @@ struct PhaseSync {
   }
 };
 
+// A level-0 coupling for the multigrid sweeps: the FP16 copy where there is one (the
+// preconditioner tolerates its rounding; the CG operator itself keeps the FP32 couplings).
+template <typename T>
+__device__ __forceinline__ T mg_coef(const T* __restrict__ c, const __half* __restrict__ h, int k) {
+  return h ? (T)__half2float(h[k]) : c[k];
+}
+
 // The CG update x += a p, r_new = r_old - a q folded into the first smoothing sweep of the
 // V-cycle that preconditions r_new (the sweep needs r_new at the neighbours, which it
 // recomputes from r_old and q there, so the separate update pass and its barrier go away).
@@ -922,6 +933,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
       T* __restrict__ r1out = mg.nu == 2 ? L.o : L.t;
       const T* __restrict__ Lidg = L.idg;
       const T* __restrict__ Lc = L.c;
+      const __half* __restrict__ Lh = l == 0 ? mg.c16 : nullptr;
       const int* __restrict__ Lnb = L.nb;
       T* __restrict__ Le = L.e;
       const int M = *L.cnt, cap = L.cap;
@@ -942,7 +954,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += Lc[f * cap + i] * (ei - w1 * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
+            s += mg_coef(Lc, Lh, f * cap + i) * (ei - w1 * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
           }
           Le[i] = ei;
           r1out[i] = bi - s;
@@ -958,7 +970,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += Lc[f * cap + i] * (ei - w1 * Lidg[j] * __ldcg(Lb + j));
+            s += mg_coef(Lc, Lh, f * cap + i) * (ei - w1 * Lidg[j] * __ldcg(Lb + j));
           }
           Le[i] = ei;
           r1out[i] = bi - s;
@@ -978,6 +990,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
         const T* __restrict__ Lo = L.o;
         const T* __restrict__ Lidg = L.idg;
         const T* __restrict__ Lc = L.c;
+        const __half* __restrict__ Lh = l == 0 ? mg.c16 : nullptr;
         const int* __restrict__ Lnb = L.nb;
         const int* __restrict__ Lagg = L.agg;
         T* __restrict__ Le = L.e;
@@ -991,7 +1004,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += Lc[f * cap + i] * (di - Lidg[j] * __ldcg(Lo + j));
+            s += mg_coef(Lc, Lh, f * cap + i) * (di - Lidg[j] * __ldcg(Lo + j));
           }
           Le[i] = __ldcg(Le + i) + w2 * di;
           atomicAdd(Cb + Lagg[i], oi - w2 * s);
@@ -1050,6 +1063,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
       const T* __restrict__ Lb = l == 0 ? b0 : L.b;
       const T* __restrict__ Lidg = L.idg;
       const T* __restrict__ Lc = L.c;
+      const __half* __restrict__ Lh = l == 0 ? mg.c16 : nullptr;
       const int* __restrict__ Lnb = L.nb;
       const int* __restrict__ Lagg = L.agg;
       const int M = *L.cnt, cap = L.cap;
@@ -1060,7 +1074,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           const int j = Lnb[f * cap + i];
-          s += Lc[f * cap + i] * (ei - (__ldcg(Le + j) + al * __ldcg(Co + Lagg[j])));
+          s += mg_coef(Lc, Lh, f * cap + i) * (ei - (__ldcg(Le + j) + al * __ldcg(Co + Lagg[j])));
         }
         const T bi = __ldcg(Lb + i);
         const T o1 = ei + (mg.nu == 2 ? w2 : w1) * Lidg[i] * (bi - s);
@@ -1075,6 +1089,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
         const T* __restrict__ Lb = l == 0 ? b0 : L.b;
         const T* __restrict__ Lidg = L.idg;
         const T* __restrict__ Lc = L.c;
+        const __half* __restrict__ Lh = l == 0 ? mg.c16 : nullptr;
         const int* __restrict__ Lnb = L.nb;
         T* __restrict__ Lo = L.o;
         const int M = *L.cnt, cap = L.cap;
@@ -1083,7 +1098,7 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
           const T ti = __ldcg(Lt + i);
           T s = 0;
 #pragma unroll
-          for (int f = 0; f < 6; ++f) s += Lc[f * cap + i] * (ti - __ldcg(Lt + Lnb[f * cap + i]));
+          for (int f = 0; f < 6; ++f) s += mg_coef(Lc, Lh, f * cap + i) * (ti - __ldcg(Lt + Lnb[f * cap + i]));
           const T bi = __ldcg(Lb + i);
           const T o2 = ti + w1 * Lidg[i] * (bi - s);
           Lo[i] = o2;

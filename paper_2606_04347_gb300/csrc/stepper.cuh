@@ -300,6 +300,7 @@ template <typename T> class Stepper : public PlanBase {
     cg_.cap = (int)g_.n;
     cg_.c = alloc<T>(6 * (size_t)g_.n);
     cg_.nb = alloc<int>(6 * (size_t)g_.n);
+    cg_.c16 = sizeof(T) == 4 ? alloc<__half>(6 * (size_t)g_.n) : nullptr;
     bmap_ = alloc<int>(g_.n);
     for (T*& h : hs_) {
       h = alloc<T>(g_.n);
@@ -708,6 +709,7 @@ template <typename T> class Stepper : public PlanBase {
       m.w2 = (T)(1.0 / (cth - rad * cq));
     }
     m.alpha = (T)1.9;
+    m.c16 = cg_.c16;
     for (int l = 0; l < mg_nlev_; ++l) {
       const HostLevel& H = lv_[l];
       MGL<T>& L = m.L[l];
