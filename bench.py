@@ -225,10 +225,10 @@ def run_ours(a):
     from paper_2606_04347_gb300 import workloads as wl
     prec = 1 if a.precision == "fp32" else 0
     p, phi0, u0, _ = wl.workload("c3", n=a.size, precision=prec)
-    # band-solve tolerance: FP64 solves to 1e-12; the FP32 form stops at 1e-5, where the
-    # FP32-vs-FP64 differences of phi, u and the energy after 20 steps at 256^3 are the same
-    # to three digits as with 1e-6 (they are set by FP32 rounding, not by the solve)
-    p = p.replace(cg_rtol=1e-5 if prec else 1e-12)
+    # band-solve tolerance: FP64 solves to 1e-12; the FP32 form stops at 1e-5 (1e-4 for the
+    # ETDRK2 predictor's solves), where the FP32-vs-FP64 differences of phi, u and the energy
+    # after 20 steps at 256^3 match those of tighter solves (they are set by FP32 rounding)
+    p = p.replace(cg_rtol=1e-5 if prec else 1e-12, cg_rtol_pred=1e-4 if prec else 0.0)
     dt_ = torch.float32 if prec else torch.float64
     stream = torch.cuda.current_stream()
     plan = Plan(p, stream=stream)
@@ -285,7 +285,7 @@ def run_ours(a):
     # FP32-mixed form and agreement of the two after the same number of steps
     fp64 = None
     if a.fp64_steps > 0 and prec == 1:
-        p64 = p.replace(precision=0, cg_rtol=1e-12)
+        p64 = p.replace(precision=0, cg_rtol=1e-12, cg_rtol_pred=0.0)
         plan64 = Plan(p64, stream=stream)
         phi64 = torch.tensor(phi0, dtype=torch.float64, device="cuda")
         u64 = torch.tensor(u0, dtype=torch.float64, device="cuda")

@@ -65,6 +65,9 @@ typedef struct {
   double cg_rtol;          /* relative residual of the band CG                         */
   int cg_maxit;            /* iteration cap of the band CG                             */
   int linear_only;         /* 1: drop R1 and R2 (the exact linear flow; tests)          */
+  double cg_rtol_pred;     /* ETDRK2 only: relative residual of the predictor-stage
+                              band solves, whose result reaches u^{n+1} only through the
+                              corrector's tau phi2 (R2(U~) - R2(U^n)) term; 0 = cg_rtol  */
 } etd_params;
 
 /* Diagnostics of the current state (Eq. (2.16) energy and the bound of Sec. 2.2). */

@@ -35,6 +35,7 @@ class etd_params(ct.Structure):
         ("A1", ct.c_double), ("A2", ct.c_double), ("B1", ct.c_double), ("B2", ct.c_double),
         ("band_mask_hi", ct.c_double), ("recover_delta", ct.c_double),
         ("cg_rtol", ct.c_double), ("cg_maxit", ct.c_int), ("linear_only", ct.c_int),
+        ("cg_rtol_pred", ct.c_double),
     ]
 
 

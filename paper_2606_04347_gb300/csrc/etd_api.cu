@@ -40,6 +40,7 @@ etd_status validate(const etd_params& p) {
   if (p.model == ETD_MODEL_COUPLED && !(p.mu > 0)) return fail(ETD_EINVAL, "mu must be positive");
   if (!(p.band_mask_hi > 0) || !(p.band_mask_hi <= 1)) return fail(ETD_EINVAL, "band_mask_hi must be in (0, 1]");
   if (!(p.cg_rtol > 0) || p.cg_maxit < 1) return fail(ETD_EINVAL, "cg_rtol > 0 and cg_maxit >= 1 required");
+  if (!(p.cg_rtol_pred >= 0)) return fail(ETD_EINVAL, "cg_rtol_pred >= 0 required");
   return ETD_OK;
 }
 

@@ -551,7 +551,7 @@ template <typename T> class Stepper : public PlanBase {
     return gs;
   }
 
-  template <typename Rhs> void cg_solve(Rhs rhs, T* x, CGGuess<T> gs = CGGuess<T>{}) {
+  template <typename Rhs> void cg_solve(Rhs rhs, T* x, CGGuess<T> gs = CGGuess<T>{}, double rtol = 0.0) {
     if (!gs.a) gs.a = x;
     CGVec<T> v = cg_;
     CGCtl c;
@@ -560,7 +560,7 @@ template <typename T> class Stepper : public PlanBase {
     c.status = status_;
     c.iters = cg_iters_;
     c.resid = cg_resid_;
-    c.rtol = P_.cg_rtol;
+    c.rtol = rtol > 0.0 ? rtol : P_.cg_rtol;
     c.maxit = P_.cg_maxit;
     c.budget = 4000000000LL;
     c.work = cg_work_;
@@ -826,7 +826,7 @@ template <typename T> class Stepper : public PlanBase {
       launch_reduce(1, u, G_, scal_ + S_MASS);
       // u-stage: new g times old u (Sec. 3.3)
       band_for_solve(nxt, G_);
-      cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_, next_guess(false, rk2));
+      cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_, next_guess(false, rk2), rk2 ? P_.cg_rtol_pred : 0.0);
       timed(ETD_K_POINTWISE, 0.0, [&] {  // bytes from the band-node counter
         k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, u, w_, scal_, hvol_, r2_,
                                                          cg_work_ + 1);
@@ -872,7 +872,7 @@ template <typename T> class Stepper : public PlanBase {
     for (int n = 0; n < nsteps; ++n) {
       ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
       launch_reduce(2, u, G_, scal_ + S_MASS);
-      cg_solve(RhsGF<T>{G_, u}, w_, next_guess(false, rk2));
+      cg_solve(RhsGF<T>{G_, u}, w_, next_guess(false, rk2), rk2 ? P_.cg_rtol_pred : 0.0);
       k_r2_fixed<T><<<grid_for(g_.n), 256, 0, st_>>>(g_, mc_, G_, mask_, u, w_, scal_, hvol_, r2_);
       fwd(ProMul<T>{G_, u}, I_[0]);
       fwd(ProLoad<T>{r2_}, I_[1]);

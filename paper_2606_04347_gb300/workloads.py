@@ -58,6 +58,7 @@ class ModelParams:
     cg_rtol: float = 1e-13
     cg_maxit: int = 20000
     linear_only: int = 0             # test mode: nonlinear terms R1 = R2 = 0
+    cg_rtol_pred: float = 0.0        # ETDRK2 predictor-stage band solves (0: cg_rtol)
 
     @property
     def shape(self):

@@ -134,14 +134,15 @@ def test_energy_sums_256(prec, tol):
 
 
 def test_fp32_form_against_fp64_at_256():
-    """The FP32-mixed step against the FP64 step on the GPU, 10 ETDRK2 steps of c3 at 256^3,
+    """The FP32-mixed step (band solves as bench.py runs them) against the FP64 step on the
+    GPU, 10 ETDRK2 steps of c3 at 256^3,
     with the tolerances the benchmark reports against (u in the G-weighted norm and on the
     core {G > 0.1}; the plain-L2 figure of u is dominated by the 1/G recovery edge)."""
     p, phi, u, _ = wl.workload("c3", n=N)
     ref = Plan(p.replace(cg_rtol=1e-12))
     phi64, u64 = dev(phi, 0), dev(u, 0)
     ref.step(phi64, u64, 10)
-    plan = Plan(p.replace(precision=1, cg_rtol=1e-5))
+    plan = Plan(p.replace(precision=1, cg_rtol=1e-5, cg_rtol_pred=1e-4))
     phi32, u32 = dev(phi, 1), dev(u, 1)
     plan.step(phi32, u32, 10)
     P64, U64, P32, U32 = host(phi64), host(u64), host(phi32), host(u32)
