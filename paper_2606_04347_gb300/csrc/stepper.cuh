@@ -288,6 +288,11 @@ template <typename T> class Stepper : public PlanBase {
     mc_.dim = P_.dim;
     mc_.linear_only = P_.linear_only;
 
+    // side stream and fork/join events of the band set-up overlap
+    ETD_CUDA(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+    ETD_CUDA(cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
+    ETD_CUDA(cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming));
+
     // workspace
     for (int i = 0; i < 5; ++i) I_[i] = alloc<C>(g_.nhat);
     sphi_ = alloc<C>(g_.nhat);
@@ -392,7 +397,30 @@ template <typename T> class Stepper : public PlanBase {
   void release() {
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
+    if (fork_ev_) cudaEventDestroy(fork_ev_);
+    if (join_ev_) cudaEventDestroy(join_ev_);
+    if (side_) cudaStreamDestroy(side_);
+    fork_ev_ = join_ev_ = nullptr;
+    side_ = nullptr;
   }
+
+  // Work that depends only on phi^{n+1} and G (the band set-up) runs on a second stream
+  // while the plan stream does the reductions and the forward transform of G u^n.
+  template <typename F> void on_side_stream(F&& work) {
+    ETD_CUDA(cudaEventRecord(fork_ev_, st_));
+    ETD_CUDA(cudaStreamWaitEvent(side_, fork_ev_, 0));
+    cudaStream_t main = st_;
+    st_ = side_;
+    try {
+      work();
+    } catch (...) {
+      st_ = main;
+      throw;
+    }
+    st_ = main;
+    ETD_CUDA(cudaEventRecord(join_ev_, side_));
+  }
+  void join_side_stream() { ETD_CUDA(cudaStreamWaitEvent(st_, join_ev_, 0)); }
 
   // ------------------------------------------------------------------ launch helpers
   int grid_for(long long n) const {
@@ -821,17 +849,18 @@ template <typename T> class Stepper : public PlanBase {
         passb(pred, I_[0], I_[1], outs({I_[0]}));
       }
       inv(I_[0], EpiPhiG<T>{nxt, G_, r2_});
+      // u-stage: new g times old u (Sec. 3.3)
+      on_side_stream([&] { band_for_solve(nxt, G_); });
       ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double) * 2, st_));  // S_VOL, S_MASS
       launch_reduce(0, nxt, nullptr, scal_ + S_VOL);
       launch_reduce(1, u, G_, scal_ + S_MASS);
-      // u-stage: new g times old u (Sec. 3.3)
-      band_for_solve(nxt, G_);
+      fwd(ProMul<T>{G_, u}, I_[0]);
+      join_side_stream();
       cg_solve(RhsGU<T>{G_, u, P_.ubar}, w_, next_guess(false, rk2), rk2 ? P_.cg_rtol_pred : 0.0);
       timed(ETD_K_POINTWISE, 0.0, [&] {  // bytes from the band-node counter
         k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, u, w_, scal_, hvol_, r2_,
                                                          cg_work_ + 1);
       });
-      fwd(ProMul<T>{G_, u}, I_[0]);
       fwd(ProLoad<T>{r2_}, I_[1]);
       OpUPred<T> upred{1, sSu_, rk2 ? 1 : 0, sk_};
       passb(upred, I_[0], I_[1], outs({I_[0]}));
@@ -973,6 +1002,8 @@ template <typename T> class Stepper : public PlanBase {
   // ------------------------------------------------------------------ state
   etd_params P_;
   cudaStream_t st_;
+  cudaStream_t side_ = nullptr;
+  cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
   Geo g_{};
   ModelC<T> mc_{};
   SpecConst<T> sk_{};
