@@ -90,9 +90,12 @@ def source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(kind, grid, prec):
+def recorded_traffic(kind, grid, prec, algo_per_launch):
     """DRAM bytes per launch of a kernel class, from the committed ncu summary, if that summary
-    was taken on the kernels as they are now (same source hash); else None."""
+    was taken on the kernels as they are now (same source hash); else None.  A class whose
+    work per launch varies (the band CG: iterations x band nodes) is recorded as the ratio of
+    measured DRAM bytes to algorithmic bytes of the captured launch and scaled to this run's
+    average launch by its algorithmic bytes."""
     path = os.path.join(ROOT, "profiles", "traffic_c3.txt")
     if not os.path.exists(path):
         return None
@@ -105,7 +108,10 @@ def recorded_traffic(kind, grid, prec):
     if rec.get("source_sha256") != source_hash():
         return None
     v = rec.get(f"{kind}_{grid}_{prec}")
-    return float(v) if v is not None else None
+    if v is not None:
+        return float(v)
+    r = rec.get(f"{kind}_{grid}_{prec}_ratio")
+    return float(r) * algo_per_launch if r is not None else None
 
 
 def peaks():
@@ -362,7 +368,7 @@ def run_ours(a):
                        "band_size": d["band_size"], "cg_iters_last": d["cg_iters_last"]},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": recorded_traffic(dom, a.size, a.precision),
+                         "traffic": recorded_traffic(dom, a.size, a.precision, dbytes / max(dn, 1)),
                          "algo_bytes_per_launch": dbytes / max(dn, 1), "avg_launch_ms": dms / max(dn, 1)},
             "step_roofline": {"bound": "hbm", "bytes_per_step": step_bytes / a.steps,
                               "bytes_per_point_step": step_bytes / a.steps / npts, "achieved": step_achieved,
