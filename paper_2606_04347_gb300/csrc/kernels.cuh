@@ -954,7 +954,8 @@ __device__ __forceinline__ int mg_vcycle(const MGP<T>& mg, const CGCtl& c, T* __
 #pragma unroll
           for (int f = 0; f < 6; ++f) {
             const int j = Lnb[f * cap + i];
-            s += mg_coef(Lc, Lh, f * cap + i) * (ei - w1 * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
+            // FP32 couplings here: this sweep is gather-bound and the half loads measured slower
+            s += Lc[f * cap + i] * (ei - w1 * Lidg[j] * (__ldcg(Ro + j) - a * __ldcg(Q + j)));
           }
           Le[i] = ei;
           r1out[i] = bi - s;
