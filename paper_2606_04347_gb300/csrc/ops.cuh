@@ -1,9 +1,10 @@
 // ops.cuh -- spectral operators run inside pass B on the spectrum held in shared memory.
 //
-// Coefficient table (built in FP64 on the host, Sec. 2.2 phi-functions of Sec. 3.2
-// symbols): for every integer m = |k|^2 of the cubic box, 6 entries
-//   tab[6m + 0..2] = phi0, tau phi1, tau phi2 at z = tau l^phi(lambda_m)
-//   tab[6m + 3..5] = phi0 - 1, tau phi1, tau phi2 at z = tau l^u(lambda_m)
+// Coefficient tables (built in FP64 on the host, Sec. 2.2 phi-functions of Sec. 3.2
+// symbols): for every integer m = |k|^2 of the cubic box one row of 4 values (the fourth
+// unused, so that one aligned vector load fetches a row)
+//   tab [4m + 0..2] = phi0, tau phi1, tau phi2 at z = tau l^phi(lambda_m)
+//   tabu[4m + 0..2] = phi0 - 1, tau phi1, tau phi2 at z = tau l^u(lambda_m)
 // (phi0 - 1 = expm1(-z): the u-stage transforms the increment of G u, see OpUPred)
 // with lambda_m = -(pi/X)^2 m.
 #pragma once
@@ -12,11 +13,24 @@
 namespace etd {
 
 template <typename T> struct SpecConst {
-  const T* tab;    // 6 coefficients per m
+  const T* tab;    // phi-stage rows, 4 values per m
+  const T* tabu;   // u-stage rows, 4 values per m
   T inv_n;         // 1/(Nx Ny Nz): the inverse transform's factor
   T kscale;        // pi / X
   T ksq;           // (pi / X)^2
 };
+
+template <typename T> struct Row3 {
+  T a, b, c;
+};
+__device__ __forceinline__ Row3<float> load_row(const float* t, int m) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(t) + m);
+  return Row3<float>{v.x, v.y, v.z};
+}
+__device__ __forceinline__ Row3<double> load_row(const double* t, int m) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(t) + 2 * m);
+  return Row3<double>{v.x, v.y, __ldg(t + 4 * m + 2)};
+}
 
 template <typename T, typename C>
 __device__ __forceinline__ C deriv_mult(int o, C v, const Wave& w, const SpecConst<T>& k) {
@@ -67,12 +81,12 @@ template <typename T> struct OpPhiPred {
   __device__ void combine(int, long long ge, const Wave& w, C& s0, C& s1) const {
     const T lam = -k.ksq * (T)w.m;
     const C r1 = C{s0.x + c_lap * lam * s1.x, s0.y + c_lap * lam * s1.y};
-    const T* c = k.tab + 6 * w.m;
-    const T a0 = c[0], a1 = c[1];
+    const Row3<T> c = load_row(k.tab, w.m);
+    const T a0 = c.a, a1 = c.b;
     const C v = spec_phi[ge];
     const C pt = C{a0 * v.x + a1 * r1.x, a0 * v.y + a1 * r1.y};
     if (rk2) {
-      const T a2 = c[2];
+      const T a2 = c.c;
       spec_S[ge] = C{pt.x - a2 * r1.x, pt.y - a2 * r1.y};
     } else {
       spec_phi[ge] = pt;
@@ -94,7 +108,7 @@ template <typename T> struct OpPhiCorr {
   __device__ void combine(int, long long ge, const Wave& w, C& s0, C& s1) const {
     const T lam = -k.ksq * (T)w.m;
     const C r1 = C{s0.x + c_lap * lam * s1.x, s0.y + c_lap * lam * s1.y};
-    const T a2 = k.tab[6 * w.m + 2];
+    const T a2 = __ldg(k.tab + 4 * w.m + 2);
     const C S = spec_S[ge];
     const C p = C{S.x + a2 * r1.x, S.y + a2 * r1.y};
     spec_phi[ge] = p;
@@ -113,9 +127,9 @@ template <typename T> struct OpUPred {
   int rk2;
   SpecConst<T> k;
   __device__ void combine(int, long long ge, const Wave& w, C& s0, C& s1) const {
-    const T* c = k.tab + 6 * w.m + 3;
-    const C p = C{c[0] * s0.x + c[1] * s1.x, c[0] * s0.y + c[1] * s1.y};
-    if (rk2) spec_S[ge] = C{p.x - c[2] * s1.x, p.y - c[2] * s1.y};
+    const Row3<T> c = load_row(k.tabu, w.m);
+    const C p = C{c.a * s0.x + c.b * s1.x, c.a * s0.y + c.b * s1.y};
+    if (rk2) spec_S[ge] = C{p.x - c.c * s1.x, p.y - c.c * s1.y};
     s0 = p;
   }
   __device__ C out(int, C v, const Wave&) const { return cscale(v, k.inv_n); }
@@ -129,7 +143,7 @@ template <typename T> struct OpUCorr {
   const C* spec_S;
   SpecConst<T> k;
   __device__ void combine(int, long long ge, const Wave& w, C& s0, C&) const {
-    const T b2 = k.tab[6 * w.m + 5];
+    const T b2 = __ldg(k.tabu + 4 * w.m + 2);
     const C S = spec_S[ge];
     s0 = C{S.x + b2 * s0.x, S.y + b2 * s0.y};
   }

@@ -341,7 +341,7 @@ template <typename T> class Stepper : public PlanBase {
     twz_ = upload_twiddles(nz);
     const double ks = M_PI / P_.half_len[0];
     const int mmax = (nx / 2) * (nx / 2) + (ny / 2) * (ny / 2) + (nz / 2) * (nz / 2);
-    std::vector<T> tab(6 * (size_t)(mmax + 1));
+    std::vector<T> tab(4 * (size_t)(mmax + 1), (T)0), tabu(4 * (size_t)(mmax + 1), (T)0);
     const double e2 = P_.eps_phi * P_.eps_phi;
     for (int m = 0; m <= mmax; ++m) {
       const double lam = -ks * ks * m;
@@ -352,17 +352,21 @@ template <typename T> class Stepper : public PlanBase {
       double a0, a1, a2, b0, b1, b2;
       phi_functions(P_.tau * lphi, a0, a1, a2);
       phi_functions(P_.tau * lu, b0, b1, b2);
-      T* t = tab.data() + 6 * (size_t)m;
+      T* t = tab.data() + 4 * (size_t)m;
       t[0] = (T)a0;
       t[1] = (T)(P_.tau * a1);
       t[2] = (T)(P_.tau * a2);
-      t[3] = (T)std::expm1(-P_.tau * lu);  // phi0 - 1: the u-stage is advanced as an increment
-      t[4] = (T)(P_.tau * b1);
-      t[5] = (T)(P_.tau * b2);
+      T* tu = tabu.data() + 4 * (size_t)m;
+      tu[0] = (T)std::expm1(-P_.tau * lu);  // phi0 - 1: the u-stage is advanced as an increment
+      tu[1] = (T)(P_.tau * b1);
+      tu[2] = (T)(P_.tau * b2);
     }
     tab_ = alloc<T>(tab.size());
+    tabu_ = alloc<T>(tabu.size());
     ETD_CUDA(cudaMemcpy(tab_, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
+    ETD_CUDA(cudaMemcpy(tabu_, tabu.data(), sizeof(T) * tabu.size(), cudaMemcpyHostToDevice));
     sk_.tab = tab_;
+    sk_.tabu = tabu_;
     sk_.inv_n = (T)(1.0 / (double)g_.n);
     sk_.kscale = (T)ks;
     sk_.ksq = (T)(ks * ks);
@@ -1033,6 +1037,7 @@ template <typename T> class Stepper : public PlanBase {
   int *idx_ = nullptr, *idx_old_ = nullptr, *bcount_ = nullptr, *count_ = nullptr, *count_old_ = nullptr;
   int nblk_ = 0;
   T* tab_ = nullptr;
+  T* tabu_ = nullptr;
   C *twx_ = nullptr, *twy_ = nullptr, *twz_ = nullptr;
   double *scal_ = nullptr, *acc_ = nullptr, *cg_resid_ = nullptr;
   unsigned* bar_ = nullptr;
