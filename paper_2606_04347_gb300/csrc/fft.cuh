@@ -429,6 +429,12 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typ
       }
       v[r] = C{A.x - B.y, A.y + B.x};
     }
+    if (ok && Epi::kPrefetch) {
+      const long long p0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx;
+      const long long p1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx;
+      const int nl = N >= 32 ? N / 32 : 1;
+      for (int q = t; q < 2 * nl; q += S) epi.prefetch((q < nl ? p0 : p1) + 32 * (q % nl));
+    }
     // the pair's rows, now held in registers, serve as the exchange scratch
     team_fft<C, R, S, true>(v, t, ra, twx, ok);
     if (ok) {

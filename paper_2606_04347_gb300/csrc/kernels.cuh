@@ -134,6 +134,8 @@ template <typename T> struct ProMul {
   __device__ T operator()(long long i) const { return a[i] * b[i]; }
 };
 template <typename T> struct EpiStore {
+  static constexpr bool kPrefetch = false;
+  __device__ void prefetch(long long) const {}
   T* out;
   __device__ void operator()(long long i, T v) const { out[i] = v; }
 };
@@ -145,7 +147,14 @@ template <typename T> struct EpiStore {
 __device__ __forceinline__ float div_inc(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double div_inc(double a, double b) { return a / b; }
 
+// Epilogues with inputs of their own (EpiRecover) prefetch their cache lines into L2 before
+// the inverse x transform of a row pair, so the loads after it find them on chip.
 template <typename T> struct EpiRecover {
+  static constexpr bool kPrefetch = true;
+  __device__ void prefetch(long long i) const {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(G + i));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + i));
+  }
   T* out;
   const T* G;
   const T* base;
@@ -159,6 +168,8 @@ template <typename T> struct EpiRecover {
 };
 // phi^{n+1} and G^{n+1} = 18 (phi^2 - phi)^2 (Algorithm 1).
 template <typename T> struct EpiPhiG {
+  static constexpr bool kPrefetch = false;
+  __device__ void prefetch(long long) const {}
   T* phi;
   T* G;
   T* zero;   // optional: a field cleared in the same pass (the band-list R2 fills its band later)
