@@ -426,6 +426,14 @@ template <typename T> class Stepper : public PlanBase {
   }
   void join_side_stream() { ETD_CUDA(cudaStreamWaitEvent(st_, join_ev_, 0)); }
 
+  // Two independent groups of launches, the first on the plan stream and the second on the
+  // side stream: the last wave of one kernel overlaps the other's instead of idling SMs.
+  template <typename A, typename B> void concurrently(A&& on_main, B&& on_side) {
+    on_side_stream(on_side);
+    on_main();
+    join_side_stream();
+  }
+
   // ------------------------------------------------------------------ launch helpers
   int grid_for(long long n) const {
     const long long b = (n + 255) / 256;
@@ -790,10 +798,15 @@ template <typename T> class Stepper : public PlanBase {
     const int nd = g_.nz > 1 ? 4 : 3;
     OpDeriv<T> op{nd, {1, 2, 3, 4, 0}, spec, sk_};
     passb(op, nullptr, nullptr, outs({I_[0], I_[1], I_[2], I_[3]}));
-    inv(I_[0], EpiStore<T>{lap_});
-    inv(I_[1], EpiStore<T>{gx_});
-    inv(I_[2], EpiStore<T>{gy_});
-    if (nd == 4) inv(I_[3], EpiStore<T>{gz_});
+    concurrently(
+        [&] {
+          inv(I_[0], EpiStore<T>{lap_});
+          inv(I_[2], EpiStore<T>{gy_});
+        },
+        [&] {
+          inv(I_[1], EpiStore<T>{gx_});
+          if (nd == 4) inv(I_[3], EpiStore<T>{gz_});
+        });
   }
 
   // R1 parts at (phi, u): rr_ = R1 without the Laplacian term, wm_ = W'(phi) - A1 phi.
@@ -831,21 +844,24 @@ template <typename T> class Stepper : public PlanBase {
       // phi-stage predictor: R1(phi^n, u^n)
       derivs(sphi_, cur);
       phi_terms(cur, u);
-      fwd(ProLoad<T>{rr_}, I_[0]);
-      fwd(ProLoad<T>{wm_}, I_[1]);
+      concurrently([&] { fwd(ProLoad<T>{rr_}, I_[0]); }, [&] { fwd(ProLoad<T>{wm_}, I_[1]); });
       if (rk2) {
         OpPhiPred<T> pred{1 + nd, {0, 1, 2, 3, 4}, sphi_, sS_, 1, c_lap_, sk_};
         passb(pred, I_[0], I_[1], outs({I_[0], I_[1], I_[2], I_[3], I_[4]}));
-        inv(I_[0], EpiStore<T>{phit_});
-        inv(I_[1], EpiStore<T>{lap_});
-        inv(I_[2], EpiStore<T>{gx_});
-        inv(I_[3], EpiStore<T>{gy_});
-        if (nd == 4) inv(I_[4], EpiStore<T>{gz_});
-        ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
-        launch_reduce(0, phit_, nullptr, scal_ + S_VOL);
+        concurrently(
+            [&] {
+              inv(I_[0], EpiStore<T>{phit_});
+              ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
+              launch_reduce(0, phit_, nullptr, scal_ + S_VOL);
+              inv(I_[2], EpiStore<T>{gx_});
+            },
+            [&] {
+              inv(I_[1], EpiStore<T>{lap_});
+              inv(I_[3], EpiStore<T>{gy_});
+              if (nd == 4) inv(I_[4], EpiStore<T>{gz_});
+            });
         phi_terms(phit_, u);  // R1(phi~, u^n): u frozen at u^n in the corrector (Sec. 3.3)
-        fwd(ProLoad<T>{rr_}, I_[0]);
-        fwd(ProLoad<T>{wm_}, I_[1]);
+        concurrently([&] { fwd(ProLoad<T>{rr_}, I_[0]); }, [&] { fwd(ProLoad<T>{wm_}, I_[1]); });
         OpPhiCorr<T> corr{1, sphi_, sS_, c_lap_, sk_};
         passb(corr, I_[0], I_[1], outs({I_[0]}));
       } else {
