@@ -569,7 +569,11 @@ __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, 
     }
   }
   __syncthreads();
+  // Outputs alternate between the two tiles, so that the row stage of output o+1 (writing
+  // one tile) may run while other threads still read the other tile in the column stage of
+  // output o: one block barrier per output.
   for (int o = 0; o < op.nout; ++o) {
+    C* tb = (o & 1) ? tile1 : tile0;
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
       const int row = rowid[rr];
@@ -581,7 +585,7 @@ __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, 
         const int kz = t + S * k;
         v[k] = ok ? op.out(o, base[rr][k], make_wave(g, kx0 + kxl, k2 + g.Y2 * k1, kz)) : C{0, 0};
       }
-      C* r0 = tile0 + (ok ? row : 0) * rs;
+      C* r0 = tb + (ok ? row : 0) * rs;
       team_fft<C, R, S, true>(v, t, r0, twz, ok);
       __syncwarp();
       if (ok) {
@@ -590,8 +594,7 @@ __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, 
       }
     }
     __syncthreads();
-    passB_cols_any<T, true>(g, kbn, nullptr, cb, tile0, rs, outs.p[o]);
-    __syncthreads();
+    passB_cols_any<T, true>(g, kbn, nullptr, cb, tb, rs, outs.p[o]);
   }
 }
 

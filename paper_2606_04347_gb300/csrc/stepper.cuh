@@ -501,7 +501,7 @@ template <typename T> class Stepper : public PlanBase {
 
   template <typename Op> void passb(const Op& op, const C* in0, const C* in1, OutP<C> o) {
     auto k = passB<T, Op>;
-    const size_t smemB = (Op::NI >= 2 ? 2 : 1) * smemB1_;
+    const size_t smemB = (Op::NI >= 2 || op.nout >= 2 ? 2 : 1) * smemB1_;  // two tiles: inputs, alternating outputs
     set_smem((const void*)k, smemB);
     const int nkb = (g_.nxh + g_.KB - 1) / g_.KB;
     timed(ETD_K_FFT_B, (Op::NI + op.nout + op_extra(op)) * spc(), [&] {
