@@ -267,6 +267,17 @@ __device__ __forceinline__ Wave make_wave(const Geo& g, int kx, int ky, int kz) 
 }
 
 
+// Inverse pass-A epilogues: epi(i, v) stores output i.  One with kSums also adds terms to
+// the partial sums of a row pair (Epi::Part, live only while the pair is stored), which
+// fold() moves into the thread's FP64 accumulators (Epi::Acc) and finish() sums over the
+// CTA when the tile is done.
+struct NoAcc {};
+template <typename Epi, typename T>
+__device__ __forceinline__ void epi_put(const Epi& e, long long i, T v, typename Epi::Part& part) {
+  if constexpr (Epi::kSums) e(i, v, part);
+  else e(i, v);
+}
+
 // Up to five output arrays of a pass-B launch, passed by value.
 template <typename C> struct OutP {
   C* p[5];
@@ -395,7 +406,8 @@ __device__ __forceinline__ void passA_cols_inv(const Geo& g, typename Cplx<T>::t
 
 template <typename T, typename Epi, int R, int S>
 __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typename Cplx<T>::type* tile, int rs,
-                                               int z0, int n1, const typename Cplx<T>::type* __restrict__ twx) {
+                                               int z0, int n1, const typename Cplx<T>::type* __restrict__ twx,
+                                               typename Epi::Acc& acc) {
   using C = typename Cplx<T>::type;
   const int t = threadIdx.x & (S - 1);
   const int team = threadIdx.x / S, nteams = blockDim.x / S;
@@ -440,12 +452,14 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typ
     if (ok) {
       const long long i0 = ((long long)(z0 + r0 / g.Y2) * g.ny + n1 + g.Y1 * (r0 % g.Y2)) * g.nx;
       const long long i1 = ((long long)(z0 + r1 / g.Y2) * g.ny + n1 + g.Y1 * (r1 % g.Y2)) * g.nx;
+      typename Epi::Part part{};
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int x = t + S * j;
-        epi(i0 + x, v[j].x);
-        epi(i1 + x, v[j].y);
+        epi_put(epi, i0 + x, v[j].x, part);
+        epi_put(epi, i1 + x, v[j].y, part);
       }
+      epi.fold(part, acc);
     }
   }
 }
@@ -467,14 +481,16 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
     default: passA_cols_inv<T, 16>(g, tile, rs, z0, n1, in, twy); break;
   }
   __syncthreads();
+  typename Epi::Acc acc{};
   switch (g.nx) {
-    case 8: passA_rows_inv<T, Epi, 8, 1>(g, epi, tile, rs, z0, n1, twx); break;
-    case 16: passA_rows_inv<T, Epi, 16, 1>(g, epi, tile, rs, z0, n1, twx); break;
-    case 32: passA_rows_inv<T, Epi, 16, 2>(g, epi, tile, rs, z0, n1, twx); break;
-    case 64: passA_rows_inv<T, Epi, 16, 4>(g, epi, tile, rs, z0, n1, twx); break;
-    case 128: passA_rows_inv<T, Epi, 16, 8>(g, epi, tile, rs, z0, n1, twx); break;
-    default: passA_rows_inv<T, Epi, 16, 16>(g, epi, tile, rs, z0, n1, twx); break;
+    case 8: passA_rows_inv<T, Epi, 8, 1>(g, epi, tile, rs, z0, n1, twx, acc); break;
+    case 16: passA_rows_inv<T, Epi, 16, 1>(g, epi, tile, rs, z0, n1, twx, acc); break;
+    case 32: passA_rows_inv<T, Epi, 16, 2>(g, epi, tile, rs, z0, n1, twx, acc); break;
+    case 64: passA_rows_inv<T, Epi, 16, 4>(g, epi, tile, rs, z0, n1, twx, acc); break;
+    case 128: passA_rows_inv<T, Epi, 16, 8>(g, epi, tile, rs, z0, n1, twx, acc); break;
+    default: passA_rows_inv<T, Epi, 16, 16>(g, epi, tile, rs, z0, n1, twx, acc); break;
   }
+  epi.finish(acc);
 }
 
 // ---- pass B: outer y DFT + z FFT, spectral operator, inverse ---------------------------

@@ -134,8 +134,12 @@ template <typename T> struct ProMul {
   __device__ T operator()(long long i) const { return a[i] * b[i]; }
 };
 template <typename T> struct EpiStore {
-  static constexpr bool kPrefetch = false;
+  static constexpr bool kPrefetch = false, kSums = false;
+  using Acc = NoAcc;
+  using Part = NoAcc;
   __device__ void prefetch(long long) const {}
+  __device__ void fold(Part&, Acc&) const {}
+  __device__ void finish(Acc&) const {}
   T* out;
   __device__ void operator()(long long i, T v) const { out[i] = v; }
 };
@@ -150,7 +154,11 @@ __device__ __forceinline__ double div_inc(double a, double b) { return a / b; }
 // Epilogues with inputs of their own (EpiRecover) prefetch their cache lines into L2 before
 // the inverse x transform of a row pair, so the loads after it find them on chip.
 template <typename T> struct EpiRecover {
-  static constexpr bool kPrefetch = true;
+  static constexpr bool kPrefetch = true, kSums = false;
+  using Acc = NoAcc;
+  using Part = NoAcc;
+  __device__ void fold(Part&, Acc&) const {}
+  __device__ void finish(Acc&) const {}
   __device__ void prefetch(long long i) const {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(G + i));
     asm volatile("prefetch.global.L2 [%0];" ::"l"(base + i));
@@ -168,8 +176,12 @@ template <typename T> struct EpiRecover {
 };
 // phi^{n+1} and G^{n+1} = 18 (phi^2 - phi)^2 (Algorithm 1).
 template <typename T> struct EpiPhiG {
-  static constexpr bool kPrefetch = false;
+  static constexpr bool kPrefetch = false, kSums = false;
+  using Acc = NoAcc;
+  using Part = NoAcc;
   __device__ void prefetch(long long) const {}
+  __device__ void fold(Part&, Acc&) const {}
+  __device__ void finish(Acc&) const {}
   T* phi;
   T* G;
   T* zero;   // optional: a field cleared in the same pass (the band-list R2 fills its band later)
@@ -368,6 +380,31 @@ template <typename T> struct CompSum {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// ubar = hi + lo in the storage precision (lo = 0 in FP64).
+template <typename T> struct Ubar {
+  T hi, lo;
+};
+template <typename T> __host__ __device__ inline Ubar<T> split_ubar(double ubar) {
+  const T hi = (T)ubar;
+  return Ubar<T>{hi, (T)(ubar - (double)hi)};
+}
+
+// One term G (x - ubar) of the mass sum.  FP32 forms it to about twice FP32 precision: ubar
+// split into hi + lo, d = x - ubar as d_hi + d_lo (two-sum with the high part, then the low
+// part), g d = rounded product + its rounding error (an FMA) + g d_lo.
+__device__ __forceinline__ void add_mass(CompSum<float>& cs, float x, float g, Ubar<float> ub) {
+  const float dh = x - ub.hi;
+  const float bp = dh - x;
+  const float dl = ((x - (dh - bp)) + (-ub.hi - bp)) - ub.lo;
+  const float pr = g * dh;
+  const float pe = fmaf(g, dh, -pr);
+  cs.add(pr);
+  cs.lo += fmaf(g, dl, pe);
+}
+__device__ __forceinline__ void add_mass(CompSum<double>& cs, double x, double g, Ubar<double> ub) {
+  cs.add(g * ((x - ub.hi) - ub.lo));
+}
+
 // mode 0: sum a ; 1: sum G (u - ubar) ; 2: sum G (f(u) - ubar).  FP64 storage sums in FP64;
 // FP32 storage forms each term to about twice FP32 precision (ubar split into hi + lo, the
 // product's rounding error from an FMA) and sums with CompSum.
@@ -384,27 +421,90 @@ __global__ void k_reduce(long long n, int mode, const T* __restrict__ a, const T
     block_add(s, dst);
     return;
   }
-  const float ub_hi = (float)ubar, ub_lo = (float)(ubar - (double)ub_hi);
+  const Ubar<float> ub = split_ubar<float>(ubar);
   CompSum<float> cs;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
     if (mode == 0) {
       cs.add((float)a[p]);
       continue;
     }
-    const float x = mode == 1 ? (float)a[p] : (float)find(a[p]);
-    const float g = (float)G[p];
-    // d = x - ubar as d_hi + d_lo (two-sum with the high part, then the low part)
-    const float dh = x - ub_hi;
-    const float bp = dh - x;
-    const float dl = ((x - (dh - bp)) + (-ub_hi - bp)) - ub_lo;
-    // g d = p + (error of the rounded product) + g d_lo
-    const float pr = g * dh;
-    const float pe = fmaf(g, dh, -pr);
-    cs.add(pr);
-    cs.lo += fmaf(g, dl, pe);
+    add_mass(cs, mode == 1 ? (float)a[p] : (float)find(a[p]), (float)G[p], ub);
   }
   block_add(cs.value(), dst);
 }
+
+// ---- inverse-transform epilogues that also form a field sum ------------------------------
+// The volume <phi, 1> and the mass sum G (u - ubar) of Sec. 3.3 (k_reduce modes 0 and 1)
+// accumulate while pass A stores the field: a compensated sum over each row pair a thread
+// stores (Part), folded into FP64 per-thread sums (Acc), one block sum per CTA added
+// atomically at the end; the field is not read back.  The caller zeroes the targets.
+template <typename T> struct Sums2 {
+  CompSum<T> s0, s1;
+};
+struct Acc2 {
+  double s0 = 0.0, s1 = 0.0;
+};
+
+template <typename T> struct EpiStoreVol {
+  static constexpr bool kPrefetch = false, kSums = true;
+  using Acc = Acc2;
+  using Part = Sums2<T>;
+  __device__ void prefetch(long long) const {}
+  T* out;
+  double* vol;
+  __device__ void operator()(long long i, T v, Part& a) const {
+    out[i] = v;
+    a.s0.add(v);
+  }
+  __device__ void fold(Part& p, Acc& a) const { a.s0 += p.s0.value(); }
+  __device__ void finish(Acc& a) const { block_add(a.s0, vol); }
+};
+
+// EpiPhiG plus the volume of phi^{n+1}.
+template <typename T> struct EpiPhiGVol {
+  static constexpr bool kPrefetch = false, kSums = true;
+  using Acc = Acc2;
+  using Part = Sums2<T>;
+  __device__ void prefetch(long long) const {}
+  T* phi;
+  T* G;
+  T* zero;
+  double* vol;
+  __device__ void operator()(long long i, T v, Part& a) const {
+    phi[i] = v;
+    G[i] = gloc(v);
+    if (zero) zero[i] = 0;
+    a.s0.add(v);
+  }
+  __device__ void fold(Part& p, Acc& a) const { a.s0 += p.s0.value(); }
+  __device__ void finish(Acc& a) const { block_add(a.s0, vol); }
+};
+
+// EpiRecover plus the mass sum of (G, u~).
+template <typename T> struct EpiRecoverMass {
+  static constexpr bool kPrefetch = true, kSums = true;
+  using Acc = Acc2;
+  using Part = Sums2<T>;
+  __device__ void prefetch(long long i) const {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(G + i));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + i));
+  }
+  T* out;
+  const T* G;
+  const T* base;
+  T delta;
+  Ubar<T> ub;
+  double* mass;
+  __device__ void operator()(long long i, T v, Part& a) const {
+    const T gg = G[i];
+    const T b = base[i];
+    const T o = gg > delta ? b + div_inc(v, gg) : gg * b + v;
+    out[i] = o;
+    add_mass(a.s0, o, gg, ub);
+  }
+  __device__ void fold(Part& p, Acc& a) const { a.s0 += p.s0.value(); }
+  __device__ void finish(Acc& a) const { block_add(a.s0, mass); }
+};
 
 // Energy terms of Eq. (2.16) except the nonlocal one, plus the bound statistics and <phi,1>.
 template <typename T>

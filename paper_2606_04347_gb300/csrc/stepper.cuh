@@ -280,6 +280,7 @@ template <typename T> class Stepper : public PlanBase {
     mc_.band_hi = (T)P_.band_mask_hi;
     mc_.delta = (T)P_.recover_delta;
     mc_.tau = (T)P_.tau;
+    ub_ = split_ubar<T>(P_.ubar);
     const double h[3] = {g_.hx, g_.hy, g_.hz};
     for (int d = 0; d < 3; ++d) {
       mc_.ih2[d] = (T)(1.0 / (h[d] * h[d]));
@@ -462,6 +463,9 @@ template <typename T> class Stepper : public PlanBase {
   static int epi_fields(const EpiStore<T>&) { return 1; }
   static int epi_fields(const EpiRecover<T>&) { return 3; }
   static int epi_fields(const EpiPhiG<T>& e) { return e.zero ? 3 : 2; }
+  static int epi_fields(const EpiStoreVol<T>&) { return 1; }
+  static int epi_fields(const EpiRecoverMass<T>&) { return 3; }
+  static int epi_fields(const EpiPhiGVol<T>& e) { return e.zero ? 3 : 2; }
 
   template <typename Pro> void fwd(Pro pro, C* out) {
     auto k = passA_fwd<T, Pro>;
@@ -850,9 +854,8 @@ template <typename T> class Stepper : public PlanBase {
         passb(pred, I_[0], I_[1], outs({I_[0], I_[1], I_[2], I_[3], I_[4]}));
         concurrently(
             [&] {
-              inv(I_[0], EpiStore<T>{phit_});
               ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
-              launch_reduce(0, phit_, nullptr, scal_ + S_VOL);
+              inv(I_[0], EpiStoreVol<T>{phit_, scal_ + S_VOL});
               inv(I_[2], EpiStore<T>{gx_});
             },
             [&] {
@@ -868,11 +871,10 @@ template <typename T> class Stepper : public PlanBase {
         OpPhiPred<T> pred{1, {0, 0, 0, 0, 0}, sphi_, sS_, 0, c_lap_, sk_};
         passb(pred, I_[0], I_[1], outs({I_[0]}));
       }
-      inv(I_[0], EpiPhiG<T>{nxt, G_, r2_});
+      ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double) * 2, st_));  // S_VOL, S_MASS
+      inv(I_[0], EpiPhiGVol<T>{nxt, G_, r2_, scal_ + S_VOL});
       // u-stage: new g times old u (Sec. 3.3)
       on_side_stream([&] { band_for_solve(nxt, G_); });
-      ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double) * 2, st_));  // S_VOL, S_MASS
-      launch_reduce(0, nxt, nullptr, scal_ + S_VOL);
       launch_reduce(1, u, G_, scal_ + S_MASS);
       fwd(ProMul<T>{G_, u}, I_[0]);
       join_side_stream();
@@ -885,9 +887,8 @@ template <typename T> class Stepper : public PlanBase {
       OpUPred<T> upred{1, sSu_, rk2 ? 1 : 0, sk_};
       passb(upred, I_[0], I_[1], outs({I_[0]}));
       if (rk2) {
-        inv(I_[0], EpiRecover<T>{ut_, G_, u, mc_.delta});
         ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
-        launch_reduce(1, ut_, G_, scal_ + S_MASS);
+        inv(I_[0], EpiRecoverMass<T>{ut_, G_, u, mc_.delta, ub_, scal_ + S_MASS});
         cg_solve(RhsGU<T>{G_, ut_, P_.ubar}, w_, next_guess(true, rk2));
         timed(ETD_K_POINTWISE, 0.0, [&] {
           k_r2_coupled_band<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, nxt, cur, ut_, w_, scal_, hvol_, r2_,
@@ -1026,6 +1027,7 @@ template <typename T> class Stepper : public PlanBase {
   cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
   Geo g_{};
   ModelC<T> mc_{};
+  Ubar<T> ub_{};
   SpecConst<T> sk_{};
   T c_lap_{};
   double hvol_ = 1.0;
