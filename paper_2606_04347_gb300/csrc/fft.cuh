@@ -524,6 +524,31 @@ __device__ __forceinline__ void passB_cols(const Geo& g, int kbn, const typename
   }
 }
 
+// Forward column stage of two inputs at once: both columns' loads are in flight together.
+template <typename T, int Y>
+__device__ __forceinline__ void passB_cols2(const Geo& g, int kbn, const typename Cplx<T>::type* src0,
+                                            const typename Cplx<T>::type* src1, long long cb,
+                                            typename Cplx<T>::type* tile0, typename Cplx<T>::type* tile1, int rs) {
+  using C = typename Cplx<T>::type;
+  const int ncols = kbn * g.nz;
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    const int kxl = col / g.nz, z = col - kxl * g.nz;
+    C v[Y > 1 ? Y : 1], w[Y > 1 ? Y : 1];
+#pragma unroll
+    for (int n1 = 0; n1 < Y; ++n1) {
+      v[n1] = src0[cb + (long long)(kxl * Y + n1) * g.nz + z];
+      w[n1] = src1[cb + (long long)(kxl * Y + n1) * g.nz + z];
+    }
+    dftN<C, Y, false>(v);
+    dftN<C, Y, false>(w);
+#pragma unroll
+    for (int k1 = 0; k1 < Y; ++k1) {
+      tile0[(kxl * Y + k1) * rs + pad16(z)] = v[k1];
+      tile1[(kxl * Y + k1) * rs + pad16(z)] = w[k1];
+    }
+  }
+}
+
 template <typename T, bool INV>
 __device__ __forceinline__ void passB_cols_any(const Geo& g, int kbn, const typename Cplx<T>::type* src, long long cb,
                                                typename Cplx<T>::type* tile, int rs, typename Cplx<T>::type* dst) {
@@ -629,8 +654,18 @@ __global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_
   const long long cb = ((long long)(k2 * g.nxh + kx0) * g.Y1) * g.nz;
   C* tile0 = reinterpret_cast<C*>(smem_raw);
   C* tile1 = tile0 + (size_t)g.KB * g.Y1 * rs;
-  if (Op::NI >= 1) passB_cols_any<T, false>(g, kbn, in0, cb, tile0, rs, nullptr);
-  if (Op::NI >= 2) passB_cols_any<T, false>(g, kbn, in1, cb, tile1, rs, nullptr);
+  // the operator's stored-spectrum reads (after the forward transforms) find their lines in L2
+  if (const C* pre = op.pre()) {
+    const int nl = (int)((size_t)kbn * g.Y1 * g.nz * sizeof(C) / 128);
+    for (int q = threadIdx.x; q < nl; q += blockDim.x)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(pre + cb) + 128 * (size_t)q));
+  }
+  if (Op::NI == 2 && g.Y1 == 16) {
+    passB_cols2<T, 16>(g, kbn, in0, in1, cb, tile0, tile1, rs);
+  } else {
+    if (Op::NI >= 1) passB_cols_any<T, false>(g, kbn, in0, cb, tile0, rs, nullptr);
+    if (Op::NI >= 2) passB_cols_any<T, false>(g, kbn, in1, cb, tile1, rs, nullptr);
+  }
   __syncthreads();
   switch (g.nz) {
     case 1: passB_rows<T, Op, 1, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;

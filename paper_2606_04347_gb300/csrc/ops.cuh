@@ -45,6 +45,7 @@ __device__ __forceinline__ C deriv_mult(int o, C v, const Wave& w, const SpecCon
 // Forward only: store the spectrum (plan layout).
 template <typename T> struct OpStore {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return nullptr; }
   static constexpr int NI = 1;
   int nout;
   C* spec;
@@ -56,6 +57,7 @@ template <typename T> struct OpStore {
 // `sel` lists the outputs (codes of deriv_mult).
 template <typename T> struct OpDeriv {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return nullptr; }
   static constexpr int NI = 0;
   int nout;
   int sel[5];
@@ -70,6 +72,7 @@ template <typename T> struct OpDeriv {
 // corrector is S + tau phi2 R1(phi~)^); ETD1 overwrites phi^ with phi~^.
 template <typename T> struct OpPhiPred {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return spec_phi; }  // stored spectrum read in combine
   static constexpr int NI = 2;
   int nout;
   int sel[5];
@@ -99,6 +102,7 @@ template <typename T> struct OpPhiPred {
 // phi-stage corrector: phi^{n+1}^ = S + tau phi2 R1(phi~)^ ; stored and emitted.
 template <typename T> struct OpPhiCorr {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return spec_S; }  // stored spectrum read in combine
   static constexpr int NI = 2;
   int nout;
   C* spec_phi;
@@ -121,6 +125,7 @@ template <typename T> struct OpPhiCorr {
 // so that GU~ = G u^n + IFFT(D~^) (EpiRecover adds G u^n back); RK2 stores S = D~^ - tau phi2 R2^.
 template <typename T> struct OpUPred {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return nullptr; }
   static constexpr int NI = 2;
   int nout;
   C* spec_S;
@@ -138,6 +143,7 @@ template <typename T> struct OpUPred {
 // u-stage corrector: GU^{n+1}^ - FFT(G u^n) = S + tau phi2 R2(U~)^.
 template <typename T> struct OpUCorr {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return spec_S; }  // stored spectrum read in combine
   static constexpr int NI = 1;
   int nout;
   const C* spec_S;
@@ -153,6 +159,7 @@ template <typename T> struct OpUCorr {
 // Standard-layout half spectrum [kz][ky][kx] in/out (operator entry points).
 template <typename T> struct OpToStd {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return nullptr; }
   static constexpr int NI = 1;
   int nout;
   C* dst;
@@ -165,6 +172,7 @@ template <typename T> struct OpToStd {
 
 template <typename T> struct OpFromStd {
   using C = typename Cplx<T>::type;
+  __device__ const C* pre() const { return nullptr; }
   static constexpr int NI = 0;
   int nout;
   const C* src;
