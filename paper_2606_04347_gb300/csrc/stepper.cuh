@@ -496,7 +496,7 @@ template <typename T> class Stepper : public PlanBase {
   // stored-spectrum traffic of each spectral operator (reads + writes of plan spectra)
   static int op_extra(const OpStore<T>&) { return 1; }
   static int op_extra(const OpDeriv<T>&) { return 1; }
-  static int op_extra(const OpPhiPred<T>& o) { return o.rk2 ? 2 : 2; }
+  static int op_extra(const OpPhiPred<T>&) { return 2; }  // phi^ read; S (RK2) or phi~^ (ETD1) written
   static int op_extra(const OpPhiCorr<T>&) { return 2; }
   static int op_extra(const OpUPred<T>& o) { return o.rk2 ? 1 : 0; }
   static int op_extra(const OpUCorr<T>&) { return 1; }
