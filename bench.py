@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=64, help="grid of the oracle sample")
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=19, help="steps of the FP64 comparison leg (0: skip)")
     return ap.parse_args()
 
@@ -130,24 +130,29 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=20):
         self.idx = gpu_index
+        self.period = period_ms
         self.proc = None
-        self.lines = []
+        self.lines = []        # (host time the sample arrived, csv line)
+        self.window = None     # (t0, t1): host times bracketing the timed region
 
     def start(self):
         exe = shutil.which("nvidia-smi")
         if not exe:
             return
         self.proc = subprocess.Popen([exe, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                      "-i", str(self.idx), "-lms", "200"],
+                                      "-i", str(self.idx), "-lms", str(self.period)],
                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def stop(self):
         if not self.proc:
@@ -160,7 +165,16 @@ class Clocks:
         self.t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        # samples that arrived while the timed region ran (one period of slack for the pipe);
+        # all samples if none did
+        lines = [ln for t, ln in self.lines]
+        scope = "whole sampler run"
+        if self.window:
+            t0, t1 = self.window
+            inside = [ln for t, ln in self.lines if t0 <= t <= t1 + self.period / 1e3]
+            if inside:
+                lines, scope = inside, "timed region"
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -175,7 +189,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "scope": scope, "period_ms": self.period}
 
 
 def oracle_sample(size, steps):
@@ -254,13 +268,16 @@ def run_ours(a):
     clk.start()
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.perf_counter()
     e0.record(stream)
     plan.step(phi, u, a.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    h1 = time.perf_counter()
     barrier()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    clk.mark(h0, h1)
     clocks = clk.stop()
     ms = allreduce_max(ms, world)
     value = aggregate(world, npts, a.steps, ms)
