@@ -39,7 +39,7 @@ typedef enum {
   ETD_ECUDA = 3,       /* a CUDA runtime call failed                                  */
   ETD_ENONFINITE = 4,  /* a non-finite value appeared in the state                    */
   ETD_ENOTCONV = 5,    /* band CG did not reach cg_rtol within cg_maxit iterations     */
-  ETD_ETIMEOUT = 6,    /* a grid-wide barrier of a persistent kernel gave up waiting   */
+  ETD_ETIMEOUT = 6,    /* a bounded device wait gave up (grid barrier, tensor copy)     */
   ETD_EMBP = 7         /* reserved: maximum bound violated beyond tolerance           */
 } etd_status;
 

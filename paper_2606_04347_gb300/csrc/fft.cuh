@@ -24,6 +24,7 @@
 // thread in registers.  Shared memory holds one padded tile per operand; twiddles come
 // from per-axis tables w_N^e = exp(-2 pi i e/N) built in FP64.
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only; the plan encodes maps through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -404,6 +405,90 @@ __device__ __forceinline__ void passA_cols_inv(const Geo& g, typename Cplx<T>::t
   }
 }
 
+// ---- TMA staging of the pass-A inverse input ------------------------------------------
+// One 4-D tensor copy per CTA brings the block's intermediate I[k2][kx][n1][z0 .. z0+ZB) into
+// shared memory (box: 2 ZB scalars x 1 x Nx/2+1 x Y2, dense, k2 slowest): the 32-byte runs of
+// the four-step layout are gathered by the copy engine instead of by 16 loads per thread.
+// Completion is tracked by an mbarrier; every wait is bounded and a copy that does not
+// complete sets the plan's status word (7) and ends the block.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier: true once it completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long tries) {
+  for (long long it = 0; it < tries; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Column stage of the inverse from the staged box: every thread first reads its column of Y
+// values (and, when ZB (Nx/2+1) exceeds the block by at most blockDim/Y columns, one value of
+// a leftover column) into registers, then the whole block writes the tile over the box.
+template <typename T, int Y>
+__device__ __forceinline__ void passA_cols_inv_staged(const Geo& g, typename Cplx<T>::type* tile, int rs, int n1,
+                                                      const typename Cplx<T>::type* __restrict__ twy) {
+  using C = typename Cplx<T>::type;
+  const C* stg = tile;
+  const int ncols = g.ZB * g.nxh, nt = blockDim.x, t = threadIdx.x;
+  const int nmain = ncols < nt ? ncols : nt, ntail = ncols - nmain;
+  C v[Y > 1 ? Y : 1];
+  const bool mine = t < nmain;
+  const int zz = t % g.ZB, kx = t / g.ZB;
+  if (mine) {
+#pragma unroll
+    for (int k2 = 0; k2 < Y; ++k2) v[k2] = stg[(k2 * g.nxh + kx) * g.ZB + zz];
+  }
+  const bool tl = t < ntail * Y;
+  const int tcol = nmain + t / Y, tk2 = t % Y;
+  C xt = C{0, 0};
+  if (tl) xt = stg[(tk2 * g.nxh + tcol / g.ZB) * g.ZB + tcol % g.ZB];
+  __syncthreads();
+  if (mine) {
+    if (n1) {
+#pragma unroll
+      for (int k2 = 1; k2 < Y; ++k2) v[k2] = cmulc(v[k2], __ldg(&twy[n1 * k2]));
+    }
+    dftN<C, Y, true>(v);
+#pragma unroll
+    for (int j = 0; j < Y; ++j) tile[(zz * Y + j) * rs + pad16(kx)] = v[j];
+  }
+  if (ntail > 0) {
+    if (tl) {
+      if (n1) xt = cmulc(xt, __ldg(&twy[n1 * tk2]));
+      tile[((tcol % g.ZB) * Y + tk2) * rs + pad16(tcol / g.ZB)] = xt;
+    }
+    __syncthreads();
+    if (t < ntail) {
+      const int col = nmain + t, z2 = col % g.ZB, k = col / g.ZB;
+#pragma unroll
+      for (int k2 = 0; k2 < Y; ++k2) v[k2] = tile[(z2 * Y + k2) * rs + pad16(k)];
+      dftN<C, Y, true>(v);
+#pragma unroll
+      for (int j = 0; j < Y; ++j) tile[(z2 * Y + j) * rs + pad16(k)] = v[j];
+    }
+  }
+}
+
 template <typename T, typename Epi, int R, int S>
 __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typename Cplx<T>::type* tile, int rs,
                                                int z0, int n1, const typename Cplx<T>::type* __restrict__ twx,
@@ -464,21 +549,57 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typ
   }
 }
 
+// Staged input of the pass-A inverse: a tensor map of the intermediate (set up by the plan
+// when the grid allows it, see Stepper::tma_map) and where the block reports a failed copy.
+struct PassAIn {
+  int tma;          // 1: stage the block's input with one tensor copy; 0: plain loads
+  uint32_t bytes;   // bytes of one staged box
+  int bar_off;      // byte offset of the mbarrier in dynamic shared memory
+  int* status;      // plan status word
+};
+
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,
                                                  const typename Cplx<T>::type* __restrict__ twx,
-                                                 const typename Cplx<T>::type* __restrict__ twy) {
+                                                 const typename Cplx<T>::type* __restrict__ twy,
+                                                 const __grid_constant__ CUtensorMap tin, PassAIn st) {
   using C = typename Cplx<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tile = reinterpret_cast<C*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smemA_raw[];
+  C* tile = reinterpret_cast<C*>(smemA_raw);
   const int rs = pitch_a(g.nx);
   const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
   const int z0 = zb * g.ZB;
-  switch (g.Y2) {
-    case 2: passA_cols_inv<T, 2>(g, tile, rs, z0, n1, in, twy); break;
-    case 4: passA_cols_inv<T, 4>(g, tile, rs, z0, n1, in, twy); break;
-    case 8: passA_cols_inv<T, 8>(g, tile, rs, z0, n1, in, twy); break;
-    default: passA_cols_inv<T, 16>(g, tile, rs, z0, n1, in, twy); break;
+  // the copy's shared-memory destination must be 128-byte aligned; otherwise load directly
+  if (st.tma && (smem_u32(tile) & 127u) == 0) {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smemA_raw + st.bar_off);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tma_load_4d(tile, &tin, 2 * z0, n1, 0, 0, bar, st.bytes);
+    }
+    const bool ok = mbar_wait(bar, 0, 1LL << 22);
+    if (__syncthreads_or(!ok)) {
+      // give the copy one more bounded chance to land before the block leaves
+      if (threadIdx.x == 0) {
+        mbar_wait(bar, 0, 1LL << 22);
+        atomicCAS(st.status, 0, 7);
+      }
+      return;
+    }
+    switch (g.Y2) {
+      case 2: passA_cols_inv_staged<T, 2>(g, tile, rs, n1, twy); break;
+      case 4: passA_cols_inv_staged<T, 4>(g, tile, rs, n1, twy); break;
+      case 8: passA_cols_inv_staged<T, 8>(g, tile, rs, n1, twy); break;
+      default: passA_cols_inv_staged<T, 16>(g, tile, rs, n1, twy); break;
+    }
+  } else {
+    switch (g.Y2) {
+      case 2: passA_cols_inv<T, 2>(g, tile, rs, z0, n1, in, twy); break;
+      case 4: passA_cols_inv<T, 4>(g, tile, rs, z0, n1, in, twy); break;
+      case 8: passA_cols_inv<T, 8>(g, tile, rs, z0, n1, in, twy); break;
+      default: passA_cols_inv<T, 16>(g, tile, rs, z0, n1, in, twy); break;
+    }
   }
   __syncthreads();
   typename Epi::Acc acc{};

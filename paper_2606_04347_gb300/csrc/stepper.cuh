@@ -1,6 +1,7 @@
 // stepper.cuh -- the plan: workspace, coefficient tables and the per-step kernel sequence
 // of Algorithm 1 (coupled model) or its frozen-membrane form (fixed model).
 #pragma once
+#include <cudaTypedefs.h>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -296,6 +297,7 @@ template <typename T> class Stepper : public PlanBase {
 
     // workspace
     for (int i = 0; i < 5; ++i) I_[i] = alloc<C>(g_.nhat);
+    tma_setup();
     sphi_ = alloc<C>(g_.nhat);
     sS_ = alloc<C>(g_.nhat);
     sSu_ = alloc<C>(g_.nhat);
@@ -478,11 +480,56 @@ template <typename T> class Stepper : public PlanBase {
 
   template <typename Epi> void inv(const C* in, Epi epi) {
     auto k = passA_inv<T, Epi>;
-    set_smem((const void*)k, smemA_);
+    const size_t smem = tma_bar_off_ + 16;
+    set_smem((const void*)k, smem);
+    PassAIn pin{0, tma_box_, (int)tma_bar_off_, status_};
+    const CUtensorMap* map = &tma_none_;
+    for (int i = 0; i < 5 && tma_ok_; ++i)
+      if (in == I_[i]) {
+        pin.tma = 1;
+        map = &tma_map_[i];
+      }
     timed(ETD_K_FFT_A_INV, spc() + epi_fields(epi) * fld(), [&] {
-      k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smemA_, st_>>>(g_, in, epi, twx_, twy_);
+      k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smem, st_>>>(g_, in, epi, twx_, twy_, *map, pin);
     });
     ETD_CUDA(cudaGetLastError());
+  }
+
+  // Tensor maps of the intermediates I_[0..4] for the pass-A inverse's staged input: 4-D
+  // (2 Nz scalars, Y1, Nx/2+1, Y2), box (2 ZB, 1, Nx/2+1, Y2).  Used when the grid is 3D, the
+  // box fits the pass-A tile, its rows are 16-byte multiples and every column of the box
+  // can be read into registers in one round plus a short leftover (passA_cols_inv_staged);
+  // otherwise, or if the driver does not provide the encoder, pass A loads directly.
+  void tma_setup() {
+    tma_bar_off_ = (smemA_ + 15) / 16 * 16;
+    std::memset(&tma_none_, 0, sizeof(tma_none_));
+    tma_ok_ = false;
+    const int nt = ETD_PASSA_THREADS, ncols = g_.ZB * g_.nxh;
+    const size_t box = (size_t)2 * g_.ZB * g_.nxh * g_.Y2 * sizeof(T);
+    const bool shape = g_.nz > 1 && g_.nxh <= 256 && g_.Y2 <= 256 && (2 * g_.ZB * sizeof(T)) % 16 == 0 &&
+                       box <= smemA_ && (ncols <= nt || (ncols <= 2 * nt && (ncols - nt) * g_.Y2 <= nt));
+    if (!shape) return;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return;
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * g_.nz, (cuuint64_t)g_.Y1, (cuuint64_t)g_.nxh, (cuuint64_t)g_.Y2};
+    const cuuint64_t strides[3] = {(cuuint64_t)2 * g_.nz * sizeof(T), (cuuint64_t)2 * g_.nz * g_.Y1 * sizeof(T),
+                                   (cuuint64_t)2 * g_.nz * g_.Y1 * g_.nxh * sizeof(T)};
+    const cuuint32_t boxd[4] = {(cuuint32_t)(2 * g_.ZB), 1u, (cuuint32_t)g_.nxh, (cuuint32_t)g_.Y2};
+    const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+    for (int i = 0; i < 5; ++i) {
+      const CUresult r = encode(&tma_map_[i], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                4, (void*)I_[i], dims, strides, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return;
+    }
+    tma_box_ = (uint32_t)box;
+    tma_ok_ = true;
   }
 
   static OutP<C> outs(std::initializer_list<C*> l) {
@@ -531,6 +578,7 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaMemset(status_, 0, sizeof(int)));
     if (s == 5) throw Error(ETD_ENOTCONV, "band CG did not reach cg_rtol within cg_maxit iterations");
     if (s == 6) throw Error(ETD_ETIMEOUT, "grid barrier of the band CG timed out");
+    if (s == 7) throw Error(ETD_ETIMEOUT, "a tensor copy of the FFT pass A did not complete");
     throw Error(ETD_ECUDA, "device status word set");
   }
 
@@ -1035,6 +1083,11 @@ template <typename T> class Stepper : public PlanBase {
   size_t smemA_ = 0, smemB1_ = 0;
   std::vector<void*> allocs_;
   C* I_[5] = {};
+  CUtensorMap tma_map_[5];
+  CUtensorMap tma_none_;
+  bool tma_ok_ = false;
+  uint32_t tma_box_ = 0;
+  size_t tma_bar_off_ = 0;
   C *sphi_ = nullptr, *sS_ = nullptr, *sSu_ = nullptr;
   T *phiA_ = nullptr, *phiB_ = nullptr, *phit_ = nullptr, *lap_ = nullptr, *gx_ = nullptr, *gy_ = nullptr,
     *gz_ = nullptr, *rr_ = nullptr, *wm_ = nullptr, *r2_ = nullptr, *ut_ = nullptr, *G_ = nullptr,
