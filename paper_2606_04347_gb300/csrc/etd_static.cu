@@ -10,6 +10,7 @@
 // holds until the process exits.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include "etd.h"
@@ -107,7 +108,11 @@ etd_status run(int dim, const int* n, const void* field, void* half, cudaStream_
   auto kb = etd::passB<T, etd::OpToStd<T>>;
   if (smemA > 48 * 1024) cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
   if (smemB > 48 * 1024) cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
-  ka<<<(nz / g.ZB) * g.Y1, ETD_PASSA_THREADS, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy);
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  const etd::PassAIn plain{0, 0u, 0, nullptr};  // direct stores (no tensor map here)
+  ka<<<(nz / g.ZB) * g.Y1, ETD_PASSA_THREADS, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy,
+                                                           none, plain);
   etd::OpToStd<T> op{0, static_cast<C*>(half), g.ny, g.nxh};
   etd::OutP<C> outs{};
   const int nkb = (g.nxh + g.KB - 1) / g.KB;

@@ -357,13 +357,109 @@ __device__ __forceinline__ void passA_cols_fwd(const Geo& g, const typename Cplx
   }
 }
 
+// ---- TMA staging of the pass-A intermediate -------------------------------------------
+// One 4-D tensor copy per CTA moves the block's part of the intermediate,
+// I[k2][kx][n1][z0 .. z0+ZB) (box: 2 ZB scalars x 1 x Nx/2+1 x Y2, dense, k2 slowest),
+// between shared memory and HBM: the 32-byte runs of the four-step layout are gathered or
+// scattered by the copy engine instead of by 16 loads or stores per thread.  Completion of a
+// load is tracked by an mbarrier; every wait is bounded and a copy that does not complete
+// sets the plan's status word (7) and ends the block.
+struct PassAIn {
+  int tma;          // 1: stage the block's intermediate with one tensor copy; 0: plain loads/stores
+  uint32_t bytes;   // bytes of one staged box
+  int bar_off;      // byte offset of the mbarrier (and, forward, the leftover columns) in dynamic shared memory
+  int* status;      // plan status word
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Store of a staged box; returns once the copy has read shared memory.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier: true once it completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long tries) {
+  for (long long it = 0; it < tries; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Column stage of the forward into the staged box (which overlaps the tile): the leftover
+// columns beyond one per thread are transformed first into a side buffer, then every thread
+// reads its column into registers, and after a barrier the block writes the box.
+template <typename T, int Y>
+__device__ __forceinline__ void passA_cols_fwd_staged(const Geo& g, typename Cplx<T>::type* tile, int rs, int n1,
+                                                      typename Cplx<T>::type* side,
+                                                      const typename Cplx<T>::type* __restrict__ twy) {
+  using C = typename Cplx<T>::type;
+  C* stg = tile;
+  const int ncols = g.ZB * g.nxh, nt = blockDim.x, t = threadIdx.x;
+  const int nmain = ncols < nt ? ncols : nt, ntail = ncols - nmain;
+  C v[Y > 1 ? Y : 1];
+  if (t < ntail) {
+    const int col = nmain + t, zz = col % g.ZB, kx = col / g.ZB;
+#pragma unroll
+    for (int j = 0; j < Y; ++j) v[j] = tile[(zz * Y + j) * rs + pad16(kx)];
+    dftN<C, Y, false>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < Y; ++k2) side[t * Y + k2] = (n1 && k2) ? cmul(v[k2], __ldg(&twy[n1 * k2])) : v[k2];
+  }
+  const bool mine = t < nmain;
+  const int zz = t % g.ZB, kx = t / g.ZB;
+  if (mine) {
+#pragma unroll
+    for (int j = 0; j < Y; ++j) v[j] = tile[(zz * Y + j) * rs + pad16(kx)];
+  }
+  __syncthreads();
+  if (mine) {
+    dftN<C, Y, false>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < Y; ++k2) {
+      C x = v[k2];
+      if (n1 && k2) x = cmul(x, __ldg(&twy[n1 * k2]));
+      stg[(k2 * g.nxh + kx) * g.ZB + zz] = x;
+    }
+  }
+  if (t < ntail * Y) {
+    const int tcol = nmain + t / Y, tk2 = t % Y;
+    stg[(tk2 * g.nxh + tcol / g.ZB) * g.ZB + tcol % g.ZB] = side[t];
+  }
+}
+
 template <typename T, typename Pro>
 __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_fwd(Geo g, Pro pro, typename Cplx<T>::type* __restrict__ out,
                                                  const typename Cplx<T>::type* __restrict__ twx,
-                                                 const typename Cplx<T>::type* __restrict__ twy) {
+                                                 const typename Cplx<T>::type* __restrict__ twy,
+                                                 const __grid_constant__ CUtensorMap tout, PassAIn st) {
   using C = typename Cplx<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tile = reinterpret_cast<C*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smemA_raw[];
+  C* tile = reinterpret_cast<C*>(smemA_raw);
   const int rs = pitch_a(g.nx);
   const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
   const int z0 = zb * g.ZB;
@@ -376,6 +472,20 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
     default: passA_rows_fwd<T, Pro, 16, 16>(g, pro, tile, rs, z0, n1, twx); break;
   }
   __syncthreads();
+  if (st.tma && (smem_u32(tile) & 127u) == 0) {
+    C* side = reinterpret_cast<C*>(smemA_raw + st.bar_off + 16);
+    switch (g.Y2) {
+      case 2: passA_cols_fwd_staged<T, 2>(g, tile, rs, n1, side, twy); break;
+      case 4: passA_cols_fwd_staged<T, 4>(g, tile, rs, n1, side, twy); break;
+      case 8: passA_cols_fwd_staged<T, 8>(g, tile, rs, n1, side, twy); break;
+      default: passA_cols_fwd_staged<T, 16>(g, tile, rs, n1, side, twy); break;
+    }
+    // the box's generic-proxy writes become visible to the copy engine, then one thread stores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) tma_store_4d(&tout, tile, 2 * z0, n1, 0, 0);
+    return;
+  }
   switch (g.Y2) {
     case 2: passA_cols_fwd<T, 2>(g, tile, rs, z0, n1, out, twy); break;
     case 4: passA_cols_fwd<T, 4>(g, tile, rs, z0, n1, out, twy); break;
@@ -403,42 +513,6 @@ __device__ __forceinline__ void passA_cols_inv(const Geo& g, typename Cplx<T>::t
 #pragma unroll
     for (int j = 0; j < Y; ++j) tile[(zz * Y + j) * rs + pad16(kx)] = v[j];
   }
-}
-
-// ---- TMA staging of the pass-A inverse input ------------------------------------------
-// One 4-D tensor copy per CTA brings the block's intermediate I[k2][kx][n1][z0 .. z0+ZB) into
-// shared memory (box: 2 ZB scalars x 1 x Nx/2+1 x Y2, dense, k2 slowest): the 32-byte runs of
-// the four-step layout are gathered by the copy engine instead of by 16 loads per thread.
-// Completion is tracked by an mbarrier; every wait is bounded and a copy that does not
-// complete sets the plan's status word (7) and ends the block.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Bounded wait for phase `parity` of the barrier: true once it completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long tries) {
-  for (long long it = 0; it < tries; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
 }
 
 // Column stage of the inverse from the staged box: every thread first reads its column of Y
@@ -548,15 +622,6 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typ
     }
   }
 }
-
-// Staged input of the pass-A inverse: a tensor map of the intermediate (set up by the plan
-// when the grid allows it, see Stepper::tma_map) and where the block reports a failed copy.
-struct PassAIn {
-  int tma;          // 1: stage the block's input with one tensor copy; 0: plain loads
-  uint32_t bytes;   // bytes of one staged box
-  int bar_off;      // byte offset of the mbarrier in dynamic shared memory
-  int* status;      // plan status word
-};
 
 template <typename T, typename Epi>
 __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,

@@ -471,11 +471,25 @@ template <typename T> class Stepper : public PlanBase {
 
   template <typename Pro> void fwd(Pro pro, C* out) {
     auto k = passA_fwd<T, Pro>;
-    set_smem((const void*)k, smemA_);
+    // tile, then (staged store) the leftover-column buffer after the barrier slot
+    const size_t smem = tma_bar_off_ + 16 + (size_t)ETD_PASSA_THREADS * sizeof(C);
+    set_smem((const void*)k, smem);
+    PassAIn pout{0, tma_box_, (int)tma_bar_off_, status_};
+    const CUtensorMap* map = tma_for(out, pout);
     timed(ETD_K_FFT_A_FWD, pro_reads(pro) * fld() + spc(), [&] {
-      k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smemA_, st_>>>(g_, pro, out, twx_, twy_);
+      k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smem, st_>>>(g_, pro, out, twx_, twy_, *map, pout);
     });
     ETD_CUDA(cudaGetLastError());
+  }
+
+  // The tensor map of an intermediate buffer (and pin.tma = 1), or the unused empty map.
+  const CUtensorMap* tma_for(const C* buf, PassAIn& pin) const {
+    for (int i = 0; i < 5 && tma_ok_; ++i)
+      if (buf == I_[i]) {
+        pin.tma = 1;
+        return &tma_map_[i];
+      }
+    return &tma_none_;
   }
 
   template <typename Epi> void inv(const C* in, Epi epi) {
@@ -483,19 +497,14 @@ template <typename T> class Stepper : public PlanBase {
     const size_t smem = tma_bar_off_ + 16;
     set_smem((const void*)k, smem);
     PassAIn pin{0, tma_box_, (int)tma_bar_off_, status_};
-    const CUtensorMap* map = &tma_none_;
-    for (int i = 0; i < 5 && tma_ok_; ++i)
-      if (in == I_[i]) {
-        pin.tma = 1;
-        map = &tma_map_[i];
-      }
+    const CUtensorMap* map = tma_for(in, pin);
     timed(ETD_K_FFT_A_INV, spc() + epi_fields(epi) * fld(), [&] {
       k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smem, st_>>>(g_, in, epi, twx_, twy_, *map, pin);
     });
     ETD_CUDA(cudaGetLastError());
   }
 
-  // Tensor maps of the intermediates I_[0..4] for the pass-A inverse's staged input: 4-D
+  // Tensor maps of the intermediates I_[0..4] for pass A's staged intermediate: 4-D
   // (2 Nz scalars, Y1, Nx/2+1, Y2), box (2 ZB, 1, Nx/2+1, Y2).  Used when the grid is 3D, the
   // box fits the pass-A tile, its rows are 16-byte multiples and every column of the box
   // can be read into registers in one round plus a short leftover (passA_cols_inv_staged);
