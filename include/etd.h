@@ -86,7 +86,10 @@ typedef struct {
  * builds the phi-function tables in FP64 (phi_0, tau phi_1, tau phi_2 of tau l^phi and
  * tau l^u, Sec. 3.2-3.3).  `cuda_stream` is a cudaStream_t (NULL = legacy stream).
  * Returns ETD_EINVAL for unsupported sizes or non-positive tau/eps, ETD_ENOMEM when the
- * workspace does not fit.  On failure *out is NULL. */
+ * workspace does not fit.  On failure *out is NULL.
+ * In 3D the FFT's first pass moves its four-step intermediate with tensor copies (TMA);
+ * the environment variable ETD_PASSA_DIRECT=1, read here, selects direct loads and stores
+ * instead (same arithmetic, bit-identical results; for verification). */
 etd_status etd_plan(const etd_params *params, void *cuda_stream, etd_plan_t *out);
 
 /* Advance `nsteps` steps in place (Algorithm 1; ETD1 or ETDRK2 per params.scheme).

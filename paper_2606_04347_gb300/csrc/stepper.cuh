@@ -3,6 +3,7 @@
 #pragma once
 #include <cudaTypedefs.h>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "kernels.cuh"
@@ -513,6 +514,9 @@ template <typename T> class Stepper : public PlanBase {
     tma_bar_off_ = (smemA_ + 15) / 16 * 16;
     std::memset(&tma_none_, 0, sizeof(tma_none_));
     tma_ok_ = false;
+    // ETD_PASSA_DIRECT=1 keeps the direct loads and stores (the two forms are compared in tests)
+    const char* direct = std::getenv("ETD_PASSA_DIRECT");
+    if (direct && direct[0] == '1') return;
     const int nt = ETD_PASSA_THREADS, ncols = g_.ZB * g_.nxh;
     const size_t box = (size_t)2 * g_.ZB * g_.nxh * g_.Y2 * sizeof(T);
     const bool shape = g_.nz > 1 && g_.nxh <= 256 && g_.Y2 <= 256 && (2 * g_.ZB * sizeof(T)) % 16 == 0 &&
