@@ -569,6 +569,87 @@ __global__ void k_band_count(long long n, const T* __restrict__ phi, T hi, unsig
   }
 }
 
+// The grid's band, 4 points per thread (one 16-byte load of phi per thread in FP32, one
+// 4-byte mask store): a block covers kCompactWide consecutive points.  Needs n % 4 == 0 and
+// a 16-byte aligned phi; k_band_scatter4 uses the same blocking.
+constexpr int kCompactWide = 4 * kCompactBlock;
+
+__device__ __forceinline__ void load4(const float* p, float (&f)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&f)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y;
+}
+
+template <typename T>
+__global__ void k_band_count4(long long n, const T* __restrict__ phi, T hi, unsigned char* __restrict__ mask,
+                              int* __restrict__ bcount) {
+  const long long p0 = blockIdx.x * (long long)kCompactWide + 4LL * threadIdx.x;
+  int c = 0;
+  if (p0 < n) {
+    T f[4];
+    load4(phi + p0, f);
+    uchar4 m;
+    m.x = in_band(f[0], hi) ? 1 : 0;
+    m.y = in_band(f[1], hi) ? 1 : 0;
+    m.z = in_band(f[2], hi) ? 1 : 0;
+    m.w = in_band(f[3], hi) ? 1 : 0;
+    *reinterpret_cast<uchar4*>(mask + p0) = m;
+    c = m.x + m.y + m.z + m.w;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ int wc[32];
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = (threadIdx.x < (blockDim.x >> 5)) ? wc[threadIdx.x] : 0;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = v;
+  }
+}
+
+// Index list and inverse map from the mask, 4 points per thread, ascending (kCompactWide
+// blocking, boff = exclusive block offsets).
+static __global__ void k_band_scatter4(long long n, const unsigned char* __restrict__ mask,
+                                       const int* __restrict__ boff, int* __restrict__ idx, int* __restrict__ bmap) {
+  const long long p0 = blockIdx.x * (long long)kCompactWide + 4LL * threadIdx.x;
+  uchar4 m = make_uchar4(0, 0, 0, 0);
+  if (p0 < n) m = *reinterpret_cast<const uchar4*>(mask + p0);
+  const int c = m.x + m.y + m.z + m.w;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  __shared__ int wc[32];
+  if (lane == 31) wc[wid] = inc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int v = (lane < (int)(blockDim.x >> 5)) ? wc[lane] : 0;
+    int w = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    wc[lane] = w - v;
+  }
+  __syncthreads();
+  int i = boff[blockIdx.x] + wc[wid] + inc - c;
+  const unsigned char mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (mm[e]) {
+      idx[i] = (int)(p0 + e);
+      bmap[p0 + e] = i;
+      ++i;
+    }
+}
+
 // Block counts of a uint8 mask (same blocking as k_band_count).
 static __global__ void k_mask_count(long long n, const unsigned char* __restrict__ mask, int* __restrict__ bcount) {
   const long long p = blockIdx.x * (long long)kCompactBlock + threadIdx.x;

@@ -601,6 +601,18 @@ template <typename T> class Stepper : public PlanBase {
   void compute_band(const T* phi) {
     std::swap(idx_, idx_old_);
     std::swap(count_, count_old_);
+    if (g_.n % 4 == 0 && (reinterpret_cast<uintptr_t>(phi) & 15) == 0) {
+      const int nb4 = (int)((g_.n + kCompactWide - 1) / kCompactWide);
+      timed(ETD_K_BAND, fld() + (double)g_.n, [&] {
+        k_band_count4<T><<<nb4, kCompactBlock, 0, st_>>>(g_.n, phi, mc_.band_hi, mask_, bcount_);
+      });
+      timed(ETD_K_BAND, 8.0 * nb4, [&] { k_band_scan<<<1, 1024, 0, st_>>>(nb4, bcount_, count_); });
+      timed(ETD_K_BAND, (double)g_.n, [&] {
+        k_band_scatter4<<<nb4, kCompactBlock, 0, st_>>>(g_.n, mask_, bcount_, idx_, bmap_);
+      });
+      ETD_CUDA(cudaGetLastError());
+      return;
+    }
     timed(ETD_K_BAND, fld() + (double)g_.n, [&] {
       k_band_count<T><<<nblk_, kCompactBlock, 0, st_>>>(g_.n, phi, mc_.band_hi, mask_, bcount_);
     });
