@@ -610,6 +610,25 @@ __global__ void k_band_count4(long long n, const T* __restrict__ phi, T hi, unsi
   }
 }
 
+// Block counts of a uint8 mask, 4 points per thread (kCompactWide blocking; n % 4 == 0).
+static __global__ void k_mask_count4(long long n, const unsigned char* __restrict__ mask, int* __restrict__ bcount) {
+  const long long p0 = blockIdx.x * (long long)kCompactWide + 4LL * threadIdx.x;
+  int c = 0;
+  if (p0 < n) {
+    const uchar4 m = *reinterpret_cast<const uchar4*>(mask + p0);
+    c = m.x + m.y + m.z + m.w;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ int wc[32];
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = (threadIdx.x < (blockDim.x >> 5)) ? wc[threadIdx.x] : 0;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = v;
+  }
+}
+
 // Index list and inverse map from the mask, 4 points per thread, ascending (kCompactWide
 // blocking, boff = exclusive block offsets).
 static __global__ void k_band_scatter4(long long n, const unsigned char* __restrict__ mask,

@@ -764,9 +764,16 @@ template <typename T> class Stepper : public PlanBase {
       timed(ETD_K_BAND, 0.0, [&] {
         ETD_CUDA(cudaMemsetAsync(L.mark, 0, L.cap, st_));
         k_mg_mark<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.lx, F.ly, is3d, L.lx, L.ly, L.mark);
-        k_mask_count<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount);
-        k_band_scan<<<1, 1024, 0, st_>>>(L.nblk, L.bcount, L.cnt);
-        k_band_scatter<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount, L.list, L.map);
+        if (L.cap % 4 == 0) {  // level grids are powers of two of at least 2^15 cells here
+          const int nb4 = (int)(((long long)L.cap + kCompactWide - 1) / kCompactWide);
+          k_mask_count4<<<nb4, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount);
+          k_band_scan<<<1, 1024, 0, st_>>>(nb4, L.bcount, L.cnt);
+          k_band_scatter4<<<nb4, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount, L.list, L.map);
+        } else {
+          k_mask_count<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount);
+          k_band_scan<<<1, 1024, 0, st_>>>(L.nblk, L.bcount, L.cnt);
+          k_band_scatter<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount, L.list, L.map);
+        }
         k_mg_parent<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.lx, F.ly, is3d, L.lx, L.ly, L.map, fagg);
         k_mg_coarse<T><<<nsm_ * 4, 256, 0, st_>>>(L.list, L.cnt, L.lx, L.ly, L.lz, is3d, fmark, fmap, F.lx, F.ly, fc,
                                                   F.cap, L.map, L.c, L.nb, L.idg, L.child, L.cap);
