@@ -924,6 +924,7 @@ template <typename T> struct MGP {
 // mark the cells of level l (grid lxc, lyc) holding nodes of level l-1 (grid lxf, lyf)
 __device__ __forceinline__ void mg_mark_body(const int* __restrict__ list, int M, int lxf, int lyf, int is3d,
                                              int lxc, int lyc, unsigned char* __restrict__ mark, int t0, int ns) {
+#pragma unroll 4
   for (int i = t0; i < M; i += ns) {
     const int p = list[i];
     const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
@@ -935,6 +936,7 @@ __device__ __forceinline__ void mg_mark_body(const int* __restrict__ list, int M
 __device__ __forceinline__ void mg_parent_body(const int* __restrict__ list, int M, int lxf, int lyf, int is3d,
                                                int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg,
                                                int t0, int ns) {
+#pragma unroll 4
   for (int i = t0; i < M; i += ns) {
     const int p = list[i];
     const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
@@ -955,13 +957,22 @@ __device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, in
     const int C = clist[I];
     const int X = C & mx, Y = (C >> lxc) & my, Z = C >> (lxc + lyc);
     T s[6] = {0, 0, 0, 0, 0, 0};
+    // the 8 children's marks, then their indices, then their couplings: three rounds of
+    // independent loads instead of a dependent chain per child
+    int Fk[8], jk[8];
+    unsigned char mk[8];
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int a = k & 1, b = (k >> 1) & 1, cz = k >> 2;
-      int j = -1;
-      if (is3d || cz == 0) {
-        const int F = (((2 * Z + cz) << (lxf + lyf)) | ((2 * Y + b) << lxf) | (2 * X + a));
-        if (fmark[F]) j = fmap[F];
-      }
+      Fk[k] = (((2 * Z + cz) << (lxf + lyf)) | ((2 * Y + b) << lxf) | (2 * X + a));
+      mk[k] = (is3d || cz == 0) ? fmark[Fk[k]] : (unsigned char)0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) jk[k] = mk[k] ? fmap[Fk[k]] : -1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int a = k & 1, b = (k >> 1) & 1, cz = k >> 2;
+      const int j = jk[k];
       child[k * cap + I] = j;
       if (j < 0) continue;
       s[a ? 0 : 1] += fc[(a ? 0 : 1) * fcap + j];
@@ -972,6 +983,7 @@ __device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, in
                           (Z << (lxc + lyc)) | (((Y + 1) & my) << lxc) | X, (Z << (lxc + lyc)) | (((Y - 1) & my) << lxc) | X,
                           (((Z + 1) & mz) << (lxc + lyc)) | (Y << lxc) | X, (((Z - 1) & mz) << (lxc + lyc)) | (Y << lxc) | X};
     T d = 0;
+#pragma unroll
     for (int f = 0; f < 6; ++f) {
       c[f * cap + I] = s[f];
       nb[f * cap + I] = s[f] > (T)0 ? cmap[ncell[f]] : I;
@@ -1039,6 +1051,7 @@ template <typename T> __global__ void __launch_bounds__(1024) k_mg_setup_tail(MG
     const int per = (L.cap + nt - 1) / nt;
     const int lo = min(L.cap, tid * per), hi = min(L.cap, lo + per);
     int own = 0;
+#pragma unroll 4
     for (int i = lo; i < hi; ++i) own += L.mark[i];
     part[tid] = own;
     __syncthreads();
