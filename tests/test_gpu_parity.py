@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, row by row.
 
-Tolerances: FP64 paths must agree with the oracle to relative L2 1e-11 (full steps, the
-spec bar) or tighter for single operators; FP32-mixed paths to relative L2 1e-5.
+Tolerances: FP64 paths must agree with the oracle to relative L2 1e-11 (full steps) or
+tighter for single operators; FP32-mixed paths to relative L2 1e-5.
 Integer work (the band index list) is compared bit for bit, the band decision taken in
 the precision of the field on both sides.
 """
