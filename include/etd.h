@@ -73,7 +73,8 @@ typedef struct {
 /* Diagnostics of the current state (Eq. (2.16) energy and the bound of Sec. 2.2). */
 typedef struct {
   double energy;           /* E_{phi,h}[U] of Eq. (2.16), band-restricted inverse      */
-  double mass;             /* fixed: <g (f(U)-ubar),1>_h ; coupled: <g (U-ubar),1>_h    */
+  double mass;             /* etd_step: fixed <g (f(U)-ubar),1>_h, coupled <g (U-ubar),1>_h;
+                              etd_energy: <g (f(U)-ubar),1>_h (the energy term), both models */
   double max_bound;        /* max |2U-1| over {G > recover_delta}                       */
   double umin, umax;       /* min/max U over {G > recover_delta}                        */
   double volume;           /* <phi,1>_h                                                */
@@ -103,7 +104,8 @@ etd_status etd_plan(const etd_params *params, void *cuda_stream, etd_plan_t *out
 etd_status etd_step(etd_plan_t plan, void *phi, void *u, int nsteps, etd_diag *last);
 
 /* Diagnostics of (phi, u): energy of Eq. (2.16) (nonlocal term by a band solve of
- * (-Delta_{S,h}) w = g f(U) - mean), mass, bound statistics, volume.  Synchronous. */
+ * (-Delta_{S,h}) w = g f(U) - mean), the energy's mass <g (f(U) - ubar), 1>_h (both models),
+ * bound statistics, volume.  Synchronous. */
 etd_status etd_energy(etd_plan_t plan, const void *phi, const void *u, etd_diag *out);
 
 /* Release the plan and its workspace.  etd_free(NULL) returns ETD_OK. */
