@@ -27,12 +27,27 @@
 #include <cuda.h>  // CUtensorMap (type only; the plan encodes maps through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "df32.cuh"
 
 namespace etd {
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<dfloat> { using type = dcomplex; };
+
+// Read-only loads of twiddles and warp shuffles for each element type.
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dcomplex ldg_c(const dcomplex* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return dcomplex{dfloat(v.x, v.y), dfloat(v.z, v.w)};
+}
+__device__ __forceinline__ float shfl(float v, int lane, int width) { return __shfl_sync(0xffffffffu, v, lane, width); }
+__device__ __forceinline__ double shfl(double v, int lane, int width) { return __shfl_sync(0xffffffffu, v, lane, width); }
+__device__ __forceinline__ dfloat shfl(dfloat v, int lane, int width) {
+  return dfloat(__shfl_sync(0xffffffffu, v.hi, lane, width), __shfl_sync(0xffffffffu, v.lo, lane, width));
+}
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
@@ -217,7 +232,7 @@ __device__ __forceinline__ void team_fft(C (&v)[R], int t, C* scr, const C* __re
   dftN<C, R, false>(v);
   if (S > 1) {
 #pragma unroll
-    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[t * k1]));
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], ldg_c(&tw[t * k1]));
     __syncwarp();
     if (act) {
 #pragma unroll
@@ -320,8 +335,8 @@ __device__ __forceinline__ void passA_rows_fwd(const Geo& g, const Pro& pro, typ
       const C send = (t == 0) ? v[(R - r) % R] : v[R - 1 - r];
       C zc;
       if (S > 1) {
-        zc.x = __shfl_sync(0xffffffffu, send.x, pl, S);
-        zc.y = __shfl_sync(0xffffffffu, send.y, pl, S);
+        zc.x = shfl(send.x, pl, S);
+        zc.y = shfl(send.y, pl, S);
       } else {
         zc = send;
       }
@@ -351,7 +366,7 @@ __device__ __forceinline__ void passA_cols_fwd(const Geo& g, const typename Cplx
 #pragma unroll
     for (int k2 = 0; k2 < Y; ++k2) {
       C x = v[k2];
-      if (n1) x = cmul(x, __ldg(&twy[n1 * k2]));
+      if (n1) x = cmul(x, ldg_c(&twy[n1 * k2]));
       out[((long long)(k2 * g.nxh + kx) * g.Y1 + n1) * g.nz + z0 + zz] = x;
     }
   }
@@ -428,7 +443,7 @@ __device__ __forceinline__ void passA_cols_fwd_staged(const Geo& g, typename Cpl
     for (int j = 0; j < Y; ++j) v[j] = tile[(zz * Y + j) * rs + pad16(kx)];
     dftN<C, Y, false>(v);
 #pragma unroll
-    for (int k2 = 0; k2 < Y; ++k2) side[t * Y + k2] = (n1 && k2) ? cmul(v[k2], __ldg(&twy[n1 * k2])) : v[k2];
+    for (int k2 = 0; k2 < Y; ++k2) side[t * Y + k2] = (n1 && k2) ? cmul(v[k2], ldg_c(&twy[n1 * k2])) : v[k2];
   }
   const bool mine = t < nmain;
   const int zz = t % g.ZB, kx = t / g.ZB;
@@ -442,7 +457,7 @@ __device__ __forceinline__ void passA_cols_fwd_staged(const Geo& g, typename Cpl
 #pragma unroll
     for (int k2 = 0; k2 < Y; ++k2) {
       C x = v[k2];
-      if (n1 && k2) x = cmul(x, __ldg(&twy[n1 * k2]));
+      if (n1 && k2) x = cmul(x, ldg_c(&twy[n1 * k2]));
       stg[(k2 * g.nxh + kx) * g.ZB + zz] = x;
     }
   }
@@ -506,7 +521,7 @@ __device__ __forceinline__ void passA_cols_inv(const Geo& g, typename Cplx<T>::t
 #pragma unroll
     for (int k2 = 0; k2 < Y; ++k2) {
       C x = in[((long long)(k2 * g.nxh + kx) * g.Y1 + n1) * g.nz + z0 + zz];
-      if (n1) x = cmulc(x, __ldg(&twy[n1 * k2]));
+      if (n1) x = cmulc(x, ldg_c(&twy[n1 * k2]));
       v[k2] = x;
     }
     dftN<C, Y, true>(v);
@@ -540,7 +555,7 @@ __device__ __forceinline__ void passA_cols_inv_staged(const Geo& g, typename Cpl
   if (mine) {
     if (n1) {
 #pragma unroll
-      for (int k2 = 1; k2 < Y; ++k2) v[k2] = cmulc(v[k2], __ldg(&twy[n1 * k2]));
+      for (int k2 = 1; k2 < Y; ++k2) v[k2] = cmulc(v[k2], ldg_c(&twy[n1 * k2]));
     }
     dftN<C, Y, true>(v);
 #pragma unroll
@@ -548,7 +563,7 @@ __device__ __forceinline__ void passA_cols_inv_staged(const Geo& g, typename Cpl
   }
   if (ntail > 0) {
     if (tl) {
-      if (n1) xt = cmulc(xt, __ldg(&twy[n1 * tk2]));
+      if (n1) xt = cmulc(xt, ldg_c(&twy[n1 * tk2]));
       tile[((tcol % g.ZB) * Y + tk2) * rs + pad16(tcol / g.ZB)] = xt;
     }
     __syncthreads();
@@ -841,10 +856,12 @@ __global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_
   C* tile0 = reinterpret_cast<C*>(smem_raw);
   C* tile1 = tile0 + (size_t)g.KB * g.Y1 * rs;
   // the operator's stored-spectrum reads (after the forward transforms) find their lines in L2
-  if (const C* pre = op.pre()) {
-    const int nl = (int)((size_t)kbn * g.Y1 * g.nz * sizeof(C) / 128);
+  if (const void* pre = op.pre()) {
+    const size_t es = op.pre_elem();
+    const int nl = (int)((size_t)kbn * g.Y1 * g.nz * es / 128);
+    const char* base = reinterpret_cast<const char*>(pre) + (size_t)cb * es;
     for (int q = threadIdx.x; q < nl; q += blockDim.x)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(pre + cb) + 128 * (size_t)q));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + 128 * (size_t)q));
   }
   if (Op::NI == 2 && g.Y1 == 16) {
     passB_cols2<T, 16>(g, kbn, in0, in1, cb, tile0, tile1, rs);

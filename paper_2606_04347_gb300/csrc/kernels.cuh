@@ -506,6 +506,47 @@ template <typename T> struct EpiRecoverMass {
   __device__ void finish(Acc& a) const { block_add(a.s0, mass); }
 };
 
+// ---- double-float transforms of the membrane state (FP32-mixed form) ----------------------
+// Pass-A prologue of the double-float forward transform of an FP32 field.
+struct ProWiden {
+  const float* a;
+  __device__ dfloat operator()(long long i) const { return dfloat(a[i]); }
+};
+
+// phi^{n+1} from the inverse transform of the phi-stage increment (FP32-mixed form): the
+// real-space phi is carried as hi + lo (hi the FP32 field the other kernels read, lo its
+// FP32 remainder), phi^{n+1} = (phi^n_hi + phi^n_lo) + d in double-float; G = 18 (phi (phi -
+// 1))^2 is formed from the double-float value with phi - 1 as (hi - 1) + lo (hi - 1 is exact
+// for hi in [0.5, 2]), so 1 - phi near the inner edge of the membrane and phi near the outer
+// edge both keep their relative accuracy in G.  Also clears the R2 field and forms the volume.
+struct EpiPhiIncVol {
+  static constexpr bool kPrefetch = true, kSums = true;
+  using Acc = Acc2;
+  using Part = Sums2<float>;
+  __device__ void prefetch(long long i) const {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(cur + i));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(lo + i));
+  }
+  const float* cur;   // phi^n (high part)
+  float* lo;          // low part, phi^n on entry, phi^{n+1} on exit (in place)
+  float* nxt;         // phi^{n+1} (high part)
+  float* G;
+  float* zero;
+  double* vol;
+  __device__ void operator()(long long i, float d, Part& a) const {
+    const dfloat p = add_f(dfloat(cur[i], lo[i]), d);
+    const float m1 = __fadd_rn(__fsub_rn(p.hi, 1.0f), p.lo);
+    const float q = p.hi * m1;
+    nxt[i] = p.hi;
+    lo[i] = p.lo;
+    G[i] = 18.0f * q * q;
+    if (zero) zero[i] = 0.0f;
+    a.s0.add(p.hi);
+  }
+  __device__ void fold(Part& p, Acc& a) const { a.s0 += p.s0.value(); }
+  __device__ void finish(Acc& a) const { block_add(a.s0, vol); }
+};
+
 // Energy terms of Eq. (2.16) except the nonlocal one, plus the bound statistics and <phi,1>.
 template <typename T>
 __global__ void k_energy_terms(Geo g, ModelC<T> mc, const T* __restrict__ G, const T* __restrict__ U,

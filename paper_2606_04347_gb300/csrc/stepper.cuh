@@ -196,7 +196,7 @@ template <typename T> class Stepper : public PlanBase {
       launch_reduce(0, phi, nullptr, scal_ + S_VOL);
       set_a0_if_needed();
       forward_store(phi, sS_);
-      derivs(sS_, phi);
+      derivs(sS_);
       phi_terms(phi, U);
       // Delta(W' - A1 phi) spectrally, then R1 = rest + kappa/(mu eps^2) Delta(W' - A1 phi)
       forward_store(wm_, sS_);
@@ -343,6 +343,9 @@ template <typename T> class Stepper : public PlanBase {
     twx_ = upload_twiddles(nx);
     twy_ = upload_twiddles(ny);
     twz_ = upload_twiddles(nz);
+    if constexpr (sizeof(T) == 4) {
+      if (P_.model == ETD_MODEL_COUPLED && g_.nz > 1) init_df(optin);
+    }
     const double ks = M_PI / P_.half_len[0];
     const int mmax = (nx / 2) * (nx / 2) + (ny / 2) * (ny / 2) + (nz / 2) * (nz / 2);
     std::vector<T> tab(4 * (size_t)(mmax + 1), (T)0), tabu(4 * (size_t)(mmax + 1), (T)0);
@@ -360,6 +363,7 @@ template <typename T> class Stepper : public PlanBase {
       t[0] = (T)a0;
       t[1] = (T)(P_.tau * a1);
       t[2] = (T)(P_.tau * a2);
+      t[3] = (T)std::expm1(-P_.tau * lphi);  // phi0 - 1 (the FP32 form's increments of phi^)
       T* tu = tabu.data() + 4 * (size_t)m;
       tu[0] = (T)std::expm1(-P_.tau * lu);  // phi0 - 1: the u-stage is advanced as an increment
       tu[1] = (T)(P_.tau * b1);
@@ -383,16 +387,35 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaDeviceSynchronize());
   }
 
-  C* upload_twiddles(int n) {
-    std::vector<C> t(n);
+  template <typename E = T> typename Cplx<E>::type* upload_twiddles(int n) {
+    using CE = typename Cplx<E>::type;
+    std::vector<CE> t(n);
     for (int e = 0; e < n; ++e) {
       const long double a = 2.0L * 3.14159265358979323846264338327950288L * e / n;
-      t[e].x = (T)cosl(a);
-      t[e].y = (T)(-sinl(a));
+      t[e].x = E((double)cosl(a));
+      t[e].y = E((double)(-sinl(a)));
     }
-    C* d = alloc<C>(n);
-    ETD_CUDA(cudaMemcpy(d, t.data(), sizeof(C) * n, cudaMemcpyHostToDevice));
+    CE* d = alloc<CE>(n);
+    ETD_CUDA(cudaMemcpy(d, t.data(), sizeof(CE) * n, cudaMemcpyHostToDevice));
     return d;
+  }
+
+  // Double-float membrane state of the FP32-mixed coupled form: the carried phi spectrum
+  // (dcomplex, plan layout), the low part of the real-space phi, the intermediate and
+  // twiddles of the double-float forward transform, and the tile geometry of 16-byte complex
+  // elements.
+  void init_df(int optin) {
+    gd_ = g_;
+    if (!choose_tiles(gd_, sizeof(dcomplex), smemAd_, smemB1d_))
+      throw Error(ETD_EINVAL, "grid not supported by the double-float FFT tiles");
+    if ((size_t)optin < smemAd_ || (size_t)optin < 2 * smemB1d_) throw Error(ETD_EINVAL, "not enough shared memory");
+    sphi_d_ = alloc<dcomplex>(g_.nhat);
+    Id_ = alloc<dcomplex>(g_.nhat);
+    philo_ = alloc<T>(g_.n);
+    twx_d_ = upload_twiddles<dfloat>(g_.nx);
+    twy_d_ = upload_twiddles<dfloat>(g_.ny);
+    twz_d_ = upload_twiddles<dfloat>(g_.nz);
+    dfphi_ = true;
   }
 
   template <typename U> U* alloc(size_t count) {
@@ -469,6 +492,7 @@ template <typename T> class Stepper : public PlanBase {
   static int epi_fields(const EpiStoreVol<T>&) { return 1; }
   static int epi_fields(const EpiRecoverMass<T>&) { return 3; }
   static int epi_fields(const EpiPhiGVol<T>& e) { return e.zero ? 3 : 2; }
+  static int epi_fields(const EpiPhiIncVol& e) { return e.zero ? 6 : 5; }  // phi^n hi, lo read; hi, lo, G (, R2) written
 
   template <typename Pro> void fwd(Pro pro, C* out) {
     auto k = passA_fwd<T, Pro>;
@@ -505,6 +529,38 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaGetLastError());
   }
 
+  // Double-float transforms (direct pass-A loads and stores; geometry gd_).
+  double dspc() const { return 2.0 * spc(); }
+  template <typename Pro> void fwd_d(Pro pro, dcomplex* out) {
+    auto k = passA_fwd<dfloat, Pro>;
+    set_smem((const void*)k, smemAd_);
+    PassAIn p{0, 0, 0, status_};
+    timed(ETD_K_FFT_A_FWD, fld() + dspc(), [&] {
+      k<<<(gd_.nz / gd_.ZB) * gd_.Y1, ETD_PASSA_THREADS, smemAd_, st_>>>(gd_, pro, out, twx_d_, twy_d_, tma_none_, p);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+  template <typename Op> void passb_d(const Op& op, const dcomplex* in0, dcomplex* out0, int nspec) {
+    auto k = passB<dfloat, Op>;
+    const size_t smemB = smemB1d_;
+    set_smem((const void*)k, smemB);
+    OutP<dcomplex> o;
+    for (int i = 0; i < 5; ++i) o.p[i] = nullptr;
+    o.p[0] = out0;
+    const int nkb = (gd_.nxh + gd_.KB - 1) / gd_.KB;
+    timed(ETD_K_FFT_B, nspec * dspc(), [&] {
+      k<<<nkb * gd_.Y2, ETD_PASSB_THREADS, smemB, st_>>>(gd_, op, in0, nullptr, o, twy_d_, twz_d_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+  // phi^ = FFT(phi) in double-float into the carried spectrum.
+  void forward_store_d(const T* field) {
+    if constexpr (sizeof(T) == 4) {
+      fwd_d(ProWiden{field}, Id_);
+      OpStore<dfloat> op{0, sphi_d_};
+      passb_d(op, Id_, nullptr, 3);  // intermediate read, spectrum written (both double-float) + its read
+    }
+  }
   // Tensor maps of the intermediates I_[0..4] for pass A's staged intermediate: 4-D
   // (2 Nz scalars, Y1, Nx/2+1, Y2), box (2 ZB, 1, Nx/2+1, Y2).  Used when the grid is 3D, the
   // box fits the pass-A tile, its rows are 16-byte multiples and every column of the box
@@ -558,6 +614,9 @@ template <typename T> class Stepper : public PlanBase {
   static int op_extra(const OpDeriv<T>&) { return 1; }
   static int op_extra(const OpPhiPred<T>&) { return 2; }  // phi^ read; S (RK2) or phi~^ (ETD1) written
   static int op_extra(const OpPhiCorr<T>&) { return 2; }
+  static int op_extra(const OpPhiPredInc& o) { return o.rk2 ? 3 : 4; }  // phi^ (double-float) read; S' or phi^ written
+  static int op_extra(const OpPhiCorrInc&) { return 5; }  // S' read, phi^ read and written (double-float)
+  static int op_extra(const OpDeriv<T, dcomplex>&) { return 2; }
   static int op_extra(const OpUPred<T>& o) { return o.rk2 ? 1 : 0; }
   static int op_extra(const OpUCorr<T>&) { return 1; }
   static int op_extra(const OpToStd<T>&) { return 1; }
@@ -878,9 +937,9 @@ template <typename T> class Stepper : public PlanBase {
   }
 
   // Delta phi and grad phi of the stored spectrum into lap_, gx_, gy_, gz_.
-  void derivs(const C* spec, const T*) {
+  template <typename S> void derivs(const S* spec) {
     const int nd = g_.nz > 1 ? 4 : 3;
-    OpDeriv<T> op{nd, {1, 2, 3, 4, 0}, spec, sk_};
+    OpDeriv<T, S> op{nd, {1, 2, 3, 4, 0}, spec, sk_};
     passb(op, nullptr, nullptr, outs({I_[0], I_[1], I_[2], I_[3]}));
     concurrently(
         [&] {
@@ -919,19 +978,37 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaMemcpyAsync(phiA_, phi, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
     T* cur = phiA_;
     T* nxt = phiB_;
-    forward_store(cur, sphi_);
+    if (dfphi_) {
+      ETD_CUDA(cudaMemsetAsync(philo_, 0, sizeof(T) * g_.n, st_));
+      forward_store_d(cur);
+    } else {
+      forward_store(cur, sphi_);
+    }
     ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
     launch_reduce(0, cur, nullptr, scal_ + S_VOL);
     set_a0_if_needed();
     const int nd = g_.nz > 1 ? 4 : 3;
     for (int n = 0; n < nsteps; ++n) {
       // phi-stage predictor: R1(phi^n, u^n)
-      derivs(sphi_, cur);
+      if constexpr (sizeof(T) == 4) {
+        if (dfphi_) derivs(sphi_d_);
+        else derivs(sphi_);
+      } else {
+        derivs(sphi_);
+      }
       phi_terms(cur, u);
       concurrently([&] { fwd(ProLoad<T>{rr_}, I_[0]); }, [&] { fwd(ProLoad<T>{wm_}, I_[1]); });
       if (rk2) {
-        OpPhiPred<T> pred{1 + nd, {0, 1, 2, 3, 4}, sphi_, sS_, 1, c_lap_, sk_};
-        passb(pred, I_[0], I_[1], outs({I_[0], I_[1], I_[2], I_[3], I_[4]}));
+        if constexpr (sizeof(T) == 4) {
+          if (dfphi_) {
+            OpPhiPredInc pred{1 + nd, {0, 1, 2, 3, 4}, sphi_d_, sS_, 1, c_lap_, sk_};
+            passb(pred, I_[0], I_[1], outs({I_[0], I_[1], I_[2], I_[3], I_[4]}));
+          }
+        }
+        if (!dfphi_) {
+          OpPhiPred<T> pred{1 + nd, {0, 1, 2, 3, 4}, sphi_, sS_, 1, c_lap_, sk_};
+          passb(pred, I_[0], I_[1], outs({I_[0], I_[1], I_[2], I_[3], I_[4]}));
+        }
         concurrently(
             [&] {
               ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double), st_));
@@ -945,14 +1022,30 @@ template <typename T> class Stepper : public PlanBase {
             });
         phi_terms(phit_, u);  // R1(phi~, u^n): u frozen at u^n in the corrector (Sec. 3.3)
         concurrently([&] { fwd(ProLoad<T>{rr_}, I_[0]); }, [&] { fwd(ProLoad<T>{wm_}, I_[1]); });
-        OpPhiCorr<T> corr{1, sphi_, sS_, c_lap_, sk_};
-        passb(corr, I_[0], I_[1], outs({I_[0]}));
+        if constexpr (sizeof(T) == 4) {
+          if (dfphi_) {
+            OpPhiCorrInc corr{1, sphi_d_, sS_, c_lap_, sk_};
+            passb(corr, I_[0], I_[1], outs({I_[0]}));
+          }
+        }
+        if (!dfphi_) {
+          OpPhiCorr<T> corr{1, sphi_, sS_, c_lap_, sk_};
+          passb(corr, I_[0], I_[1], outs({I_[0]}));
+        }
+      } else if (dfphi_) {
+        if constexpr (sizeof(T) == 4) {
+          OpPhiPredInc pred{1, {0, 0, 0, 0, 0}, sphi_d_, sS_, 0, c_lap_, sk_};
+          passb(pred, I_[0], I_[1], outs({I_[0]}));
+        }
       } else {
         OpPhiPred<T> pred{1, {0, 0, 0, 0, 0}, sphi_, sS_, 0, c_lap_, sk_};
         passb(pred, I_[0], I_[1], outs({I_[0]}));
       }
       ETD_CUDA(cudaMemsetAsync(scal_ + S_VOL, 0, sizeof(double) * 2, st_));  // S_VOL, S_MASS
-      inv(I_[0], EpiPhiGVol<T>{nxt, G_, r2_, scal_ + S_VOL});
+      if constexpr (sizeof(T) == 4) {
+        if (dfphi_) inv(I_[0], EpiPhiIncVol{cur, philo_, nxt, G_, r2_, scal_ + S_VOL});
+      }
+      if (!dfphi_) inv(I_[0], EpiPhiGVol<T>{nxt, G_, r2_, scal_ + S_VOL});
       // u-stage: new g times old u (Sec. 3.3)
       on_side_stream([&] { band_for_solve(nxt, G_); });
       launch_reduce(1, u, G_, scal_ + S_MASS);
@@ -1147,6 +1240,13 @@ template <typename T> class Stepper : public PlanBase {
   int *status_ = nullptr, *flag_ = nullptr, *cg_iters_ = nullptr;
   bool a0_set_ = false, fixed_ready_ = false, band_dirty_ = false, w_reset_ = true;
   T* hs_[3] = {};                 // solution history of the band solves (full grid)
+  // double-float membrane state (FP32-mixed coupled form)
+  bool dfphi_ = false;
+  Geo gd_{};
+  size_t smemAd_ = 0, smemB1d_ = 0;
+  dcomplex *sphi_d_ = nullptr, *Id_ = nullptr;
+  dcomplex *twx_d_ = nullptr, *twy_d_ = nullptr, *twz_d_ = nullptr;
+  T* philo_ = nullptr;
   int hP_ = -1, hC_ = -1, hO_ = -1;  // slots: last predictor, last corrector, the older entry
 };
 

@@ -135,9 +135,8 @@ def test_energy_sums_256(prec, tol):
 
 def test_fp32_form_against_fp64_at_256():
     """The FP32-mixed step (band solves as bench.py runs them) against the FP64 step on the
-    GPU, 10 ETDRK2 steps of c3 at 256^3,
-    with the tolerances the benchmark reports against (u in the G-weighted norm and on the
-    core {G > 0.1}; the plain-L2 figure of u is dominated by the 1/G recovery edge)."""
+    GPU, 10 ETDRK2 steps of c3 at 256^3 from the same input: phi, u (plain relative L2 over the
+    whole grid) and the energy within 1e-5."""
     p, phi, u, _ = wl.workload("c3", n=N)
     ref = Plan(p.replace(cg_rtol=1e-12))
     phi64, u64 = dev(phi, 0), dev(u, 0)
@@ -146,17 +145,15 @@ def test_fp32_form_against_fp64_at_256():
     phi32, u32 = dev(phi, 1), dev(u, 1)
     plan.step(phi32, u32, 10)
     P64, U64, P32, U32 = host(phi64), host(u64), host(phi32), host(u32)
-    G = omodel.g_loc(P64)
     e_phi = rel_l2(P32, P64)
-    e_ug = rel_l2(U32, U64, w=G)
-    e_core = rel_l2(U32[G > 0.1], U64[G > 0.1])
-    e_full = rel_l2(U32, U64)
-    e64 = ref.energy(phi64, u64)["energy"]
-    e32 = plan.energy(phi32, u32)["energy"]
-    print("256^3 fp32 vs fp64: phi", e_phi, "u_G", e_ug, "u core", e_core, "u full", e_full,
-          "energy", abs(e32 - e64) / abs(e64))
+    e_u = rel_l2(U32, U64)
+    d64 = ref.energy(phi64, u64)
+    d32 = plan.energy(phi32, u32)
+    e_e = abs(d32["energy"] - d64["energy"]) / abs(d64["energy"])
+    print("256^3 fp32 vs fp64: phi", e_phi, "u", e_u, "energy", e_e,
+          "max bound", d32["max_bound"], d64["max_bound"])
     assert e_phi < 1e-5
-    assert e_ug < 1e-5
-    assert e_core < 1e-5
-    assert e_full < 2e-4
-    assert abs(e32 - e64) < 1e-4 * abs(e64)
+    assert e_u < 1e-5
+    assert e_e < 1e-5
+    if d64["max_bound"] <= 1.0:
+        assert d32["max_bound"] <= 1.0 + 1e-6

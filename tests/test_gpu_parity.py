@@ -199,14 +199,8 @@ def test_coupled_matches_oracle_fp64(scheme, n, steps):
 
 
 def test_coupled_fp32_against_fp64_gpu():
-    """FP32-mixed vs FP64 on the GPU after 20 coupled ETDRK2 steps.
-
-    phi and the energy meet 1e-5.  For u the FP32 FFT leaves an absolute error of about
-    eps32 * sqrt(log2 N) * rms(GU) ~ 1e-8 in GU everywhere; the recovery U = GU/G divides it
-    by G, down to G = 1e-3 at the edge of the recovery set, so u meets 1e-5 on the membrane
-    core {G > 0.1} and only ~1e-4 on the full recovery set (a property of the scheme's
-    recovery step in FP32, measured and reported, not a tolerance of the kernels).
-    """
+    """FP32-mixed vs FP64 on the GPU after 20 coupled ETDRK2 steps from the same input:
+    phi, u (plain relative L2 over the whole grid) and the energy within 1e-5."""
     p, phi, u, _ = wl.workload("c3", n=32)
     p = p.replace(cg_rtol=1e-12)
     ref = Plan(p)
@@ -217,15 +211,17 @@ def test_coupled_fp32_against_fp64_gpu():
     phi32, u32 = dev(phi, 1), dev(u, 1)
     d = plan.step(phi32, u32, 20, diag=True)
     U64, U32 = host(u64), host(u32)
-    G = omodel.g_loc(host(phi64))
-    errs = {thr: rel_l2(U32[G > thr], U64[G > thr]) for thr in (1e-3, 1e-2, 1e-1)}
-    print("fp32 vs fp64: phi", rel_l2(host(phi32), host(phi64)), "u full", rel_l2(U32, U64), "u by G>", errs)
-    assert rel_l2(host(phi32), host(phi64)) < 1e-5
-    assert errs[1e-1] < 1e-5
-    assert rel_l2(U32, U64) < 2e-4
     e64 = ref.energy(phi64, u64)
     e32 = plan.energy(phi32, u32)
+    print("fp32 vs fp64: phi", rel_l2(host(phi32), host(phi64)), "u", rel_l2(U32, U64),
+          "energy", abs(e32["energy"] - e64["energy"]) / abs(e64["energy"]),
+          "max bound", e32["max_bound"], e64["max_bound"])
+    assert rel_l2(host(phi32), host(phi64)) < 1e-5
+    assert rel_l2(U32, U64) < 1e-5
     assert abs(e32["energy"] - e64["energy"]) < 1e-5 * abs(e64["energy"])
+    # maximum bound: where the FP64 form keeps max|2U-1| <= 1, the FP32 form stays within 1e-6
+    if e64["max_bound"] <= 1.0:
+        assert e32["max_bound"] <= 1.0 + 1e-6
     assert d["cg_resid_last"] <= 1e-6
 
 
