@@ -17,12 +17,16 @@ Contents (each module cites the passage it restates):
 
 Pins (tests marked `not gpu`): brute-force DFT and numpy.fft for the FFT; series/quadrature/
 multiprecision for phi_j; single Fourier modes (exact exponential); dense 8^2 matrix
-exponentials by scipy.linalg.expm of augmented matrices; the expansion identity
-R1 - L_phi phi = Eq. (1.1)/mu; FD identities (symmetry, summation by parts, discrete
+exponentials by scipy.linalg.expm of augmented matrices (fixed step) and dense 8^3 ones for
+one coupled ETD1/ETDRK2 step; the expansion identity R1 - L_phi phi = Eq. (1.1)/mu; the
+line-tension, area and alpha terms of R1 on single-mode membranes in closed form; R2 (fixed,
+and coupled without motion) as the negative L2 gradient of the discrete energy built from the
+dense Sec. 2 matrices; model.energy against the dense Sec. 2 energy; the advection term on a
+translated profile in closed form; FD identities (symmetry, summation by parts, discrete
 eigenvalues); sparse direct solves for the band inverse; the maximum-bound and energy
 theorems of Sec. 2.2 on dense grids; temporal orders of ETD1/ETDRK2.
 
-Parity unpinned: the fully assembled coupled step (R1 with all couplings, R2 with advection
-and the band solve, chained through Algorithm 1) has no closed form or printed value; it is
-pinned only piecewise by the identities above.
+Parity unpinned: the fully assembled coupled step over many steps (Algorithm 1 with R1, R2,
+the advection and the band solve interacting) has no closed form or printed value; each of
+its terms and one step of its driver are pinned as listed above.
 """

@@ -2,7 +2,7 @@
 
 Sec. 3.2 evaluates the nonlocal surface term only on a narrow band around the membrane and
 leaves the band threshold, the band-edge treatment and the solver open.  Readings taken
-here (listed with the others in the design notes):
+here:
 
 * band            = {|2 Phi - 1| < hi}, hi = 0.99 (equivalently g(Phi) > 4.46e-4);
 * band edge       : a face with an off-band end carries coefficient 0 (zero flux);

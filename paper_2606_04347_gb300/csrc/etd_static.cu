@@ -106,8 +106,25 @@ etd_status run(int dim, const int* n, const void* field, void* half, cudaStream_
 
   auto ka = etd::passA_fwd<T, etd::ProLoad<T>>;
   auto kb = etd::passB<T, etd::OpToStd<T>>;
-  if (smemA > 48 * 1024) cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
-  if (smemB > 48 * 1024) cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
+  int dev = 0, optin = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (ce != cudaSuccess) {
+    etd::set_last_error(std::string("shared-memory limit query: ") + cudaGetErrorString(ce));
+    return ETD_ECUDA;
+  }
+  if ((size_t)optin < smemA || (size_t)optin < smemB) {
+    etd::set_last_error("grid needs " + std::to_string(std::max(smemA, smemB)) + " bytes of shared memory per block, " +
+                        "the device allows " + std::to_string(optin));
+    return ETD_EINVAL;
+  }
+  if (smemA > 48 * 1024) ce = cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA);
+  if (ce == cudaSuccess && smemB > 48 * 1024)
+    ce = cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB);
+  if (ce != cudaSuccess) {
+    etd::set_last_error(std::string("cudaFuncSetAttribute(MaxDynamicSharedMemorySize): ") + cudaGetErrorString(ce));
+    return ETD_ECUDA;
+  }
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
   const etd::PassAIn plain{0, 0u, 0, nullptr};  // direct stores (no tensor map here)

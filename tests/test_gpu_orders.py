@@ -5,7 +5,7 @@ Sec. 2 model on the spectral split of Sec. 3, 32^2), run through the CUDA path a
 its own fine-step solution, with the oracle test's bounds on the last observed rate.
 On finer grids both the oracle and the GPU path see the ETDRK2 rate fall toward 1 over
 the same step range (identical rates at 64^2: 1.46, 1.24), the order reduction of a stiff
-problem; that is recorded in the design notes, not asserted here.
+problem, which is not asserted here.
 """
 import math
 
