@@ -40,7 +40,8 @@ typedef enum {
   ETD_ENONFINITE = 4,  /* a non-finite value appeared in the state                    */
   ETD_ENOTCONV = 5,    /* band CG did not reach cg_rtol within cg_maxit iterations     */
   ETD_ETIMEOUT = 6,    /* a bounded device wait gave up (grid barrier, tensor copy)     */
-  ETD_EMBP = 7         /* reserved: maximum bound violated beyond tolerance           */
+  ETD_EMBP = 7         /* reserved, never returned: the spectral schemes of Sec. 3 do not
+                          guarantee the maximum bound (etd_diag reports max |2U-1|)      */
 } etd_status;
 
 typedef enum { ETD_ETD1 = 1, ETD_ETDRK2 = 2 } etd_scheme;
@@ -90,7 +91,13 @@ typedef struct {
  * workspace does not fit.  On failure *out is NULL.
  * In 3D the FFT's first pass moves its four-step intermediate with tensor copies (TMA);
  * the environment variable ETD_PASSA_DIRECT=1, read here, selects direct loads and stores
- * instead (same arithmetic, bit-identical results; for verification). */
+ * instead (same arithmetic, bit-identical results; for verification).
+ * Every device wait is bounded: a grid barrier of the band solve gives up after
+ * ETD_WAIT_BUDGET clock cycles (default 4e9) and a tensor copy of the FFT after
+ * ETD_WAIT_TRIES mbarrier polls (default 2^22); both environment variables are read here.
+ * A wait that gives up makes the call that observes it return ETD_ETIMEOUT, the device
+ * context stays usable (the waiting blocks return, a block whose copy is late waits for it
+ * once more before it leaves). */
 etd_status etd_plan(const etd_params *params, void *cuda_stream, etd_plan_t *out);
 
 /* Advance `nsteps` steps in place (Algorithm 1; ETD1 or ETDRK2 per params.scheme).
@@ -131,7 +138,10 @@ etd_status etd_band(etd_plan_t plan, const void *phi, int *idx, long *count);
 
 /* Band-restricted nonlocal solve: w = (-Delta_{S,h})^{-1}(f - mean) on the band of phi
  * with zero-flux band edges, g = g(phi) (Eq. (2.3)); f and w are full fields, w = 0
- * off the band.  Warm start from the incoming w.  Synchronous; reports iterations and
+ * off the band.  The band operator is singular on each connected band component (6-neighbour,
+ * periodic), so the mean of f is removed and w is returned with zero mean on every component
+ * separately (the mean removal of Sec. 2.1, per component; up to 4096 components, more
+ * return ETD_EINVAL).  Warm start from the incoming w.  Synchronous; reports iterations and
  * relative residual. */
 etd_status etd_nonlocal(etd_plan_t plan, const void *phi, const void *f, void *w,
                         int *iters, double *resid);

@@ -127,7 +127,7 @@ etd_status run(int dim, const int* n, const void* field, void* half, cudaStream_
   }
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
-  const etd::PassAIn plain{0, 0u, 0, nullptr};  // direct stores (no tensor map here)
+  const etd::PassAIn plain{0, 0u, 0, nullptr, 0};  // direct stores (no tensor map, no wait)
   ka<<<(nz / g.ZB) * g.Y1, ETD_PASSA_THREADS, smemA, st>>>(g, etd::ProLoad<T>{static_cast<const T*>(field)}, I, twx, twy,
                                                            none, plain);
   etd::OpToStd<T> op{0, static_cast<C*>(half), g.ny, g.nxh};

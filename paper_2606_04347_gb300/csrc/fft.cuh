@@ -384,6 +384,7 @@ struct PassAIn {
   uint32_t bytes;   // bytes of one staged box
   int bar_off;      // byte offset of the mbarrier (and, forward, the leftover columns) in dynamic shared memory
   int* status;      // plan status word
+  long long tries;  // polls of the copy's mbarrier before the block gives up (default 2^22)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -658,9 +659,10 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tma_load_4d(tile, &tin, 2 * z0, n1, 0, 0, bar, st.bytes);
     }
-    const bool ok = mbar_wait(bar, 0, 1LL << 22);
+    const bool ok = mbar_wait(bar, 0, st.tries);
     if (__syncthreads_or(!ok)) {
-      // give the copy one more bounded chance to land before the block leaves
+      // the copy writes this block's shared memory: give it one more bounded chance to land
+      // before the block leaves
       if (threadIdx.x == 0) {
         mbar_wait(bar, 0, 1LL << 22);
         atomicCAS(st.status, 0, 7);

@@ -834,6 +834,270 @@ static __global__ void k_zero_left(const int* __restrict__ old_idx, const int* _
   }
 }
 
+// ---- connected components of the band (per-component mean removal of the band solve) ----
+// The band operator is singular on every connected band component (6-neighbour, periodic),
+// so the right-hand side and the solution are projected to zero mean per component (the
+// whole-domain mean removal of Sec. 2.1 applied to each component).  Components come from a
+// lock-free union-find over the band's neighbour lists: every link points from a larger node
+// index to a smaller one, so each chase follows strictly decreasing indices and ends, and a
+// failed link means another thread made progress (each loop is bounded by the node count).
+constexpr int kCompCap = 4096;   // components the band solve supports (more: status 8)
+
+__device__ __forceinline__ int cc_root(int* __restrict__ parent, int v) {
+  int cur = __ldcg(parent + v);
+  if (cur == v) return v;
+  int prev = v;
+  for (;;) {
+    const int next = __ldcg(parent + cur);
+    if (next >= cur) break;                // cur is a root (parent[cur] == cur)
+    parent[prev] = next;                   // path halving; the value only ever decreases
+    prev = cur;
+    cur = next;
+  }
+  return cur;
+}
+
+// Each node starts as a child of its smallest band neighbour (or of itself), which leaves a
+// forest with one tree per local minimum of the index over the band; linking then only has to
+// merge those trees.
+template <typename T>
+__global__ void k_cc_init(const int* __restrict__ count, CGVec<T> v, int* __restrict__ parent, const int* fallback) {
+  if (!*fallback) return;
+  const int M = *count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    int m = i;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) m = min(m, v.nb[f * v.cap + i]);
+    parent[i] = m;
+  }
+}
+
+template <typename T>
+__global__ void k_cc_link(const int* __restrict__ count, CGVec<T> v, int* __restrict__ parent, int* status,
+                          const int* fallback) {
+  if (!*fallback) return;
+  const int M = *count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int f = 0; f < 6; f += 2) {       // the + faces: every band edge is seen from one end
+      const int j = v.nb[f * v.cap + i];
+      if (j == i) continue;
+      int a = cc_root(parent, i), b = cc_root(parent, j);
+      for (int tries = 0; a != b; ++tries) {
+        if (tries > M) {                   // cannot happen; guards the loop bound
+          atomicCAS(status, 0, 8);
+          return;
+        }
+        const int hi = a > b ? a : b, lo = a > b ? b : a;
+        const int old = atomicCAS(parent + hi, hi, lo);
+        if (old == hi) break;
+        a = cc_root(parent, old);
+        b = lo;
+      }
+    }
+  }
+}
+
+// Full compression and a compact id per root (arbitrary order).
+static __global__ void k_cc_roots(const int* __restrict__ count, int* __restrict__ parent, int* __restrict__ cid,
+                                  int* __restrict__ ncomp, const int* fallback) {
+  if (!*fallback) return;
+  const int M = *count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int r = cc_root(parent, i);
+    parent[i] = r;
+    if (r == i) cid[i] = atomicAdd(ncomp, 1);
+  }
+}
+
+// Per-component sums of one pass over the band: components below kCompShared accumulate in
+// shared memory (one global atomic per block and component), others per warp group (lanes
+// holding the same component combine their values, one atomic per group).  Every thread of
+// the block calls begin() and end(); add() may be called under divergence.
+constexpr int kCompShared = 64;
+struct CompAcc {
+  double* sh;    // kCompShared doubles of shared memory
+  double* dst;   // global accumulators, one per component
+  int C;
+  __device__ void begin() {
+    for (int k = threadIdx.x; k < kCompShared; k += blockDim.x) sh[k] = 0.0;
+    __syncthreads();
+  }
+  __device__ void add(int c, double v) {
+    if (c < kCompShared) {
+      atomicAdd(sh + c, v);
+      return;
+    }
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, c);
+    double s = 0.0;
+    for (unsigned m = grp; m; m &= m - 1) s += __shfl_sync(grp, v, __ffs(m) - 1);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(dst + c, s);
+  }
+  __device__ void end() {
+    __syncthreads();
+    const int n = C < kCompShared ? C : kCompShared;
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+      if (sh[k] != 0.0) atomicAdd(dst + k, sh[k]);
+    __syncthreads();
+  }
+};
+
+// Node components and component sizes.  A band of one component needs neither: the solve
+// then removes the plain mean, and only the size is written.
+static __global__ void k_cc_label(const int* __restrict__ count, const int* __restrict__ parent,
+                                  const int* __restrict__ cid, const int* __restrict__ ncomp, int* __restrict__ comp,
+                                  double* __restrict__ csize, int* status, const int* fallback) {
+  __shared__ double sh[kCompShared];
+  if (!*fallback) return;
+  const int M = *count;
+  const int C = *ncomp;
+  if (C > kCompCap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(status, 0, 8);
+    return;
+  }
+  if (C <= 1) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) csize[0] = (double)M;
+    return;
+  }
+  CompAcc acc{sh, csize, C};
+  acc.begin();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int c = cid[parent[i]];
+    comp[i] = c;
+    acc.add(c, 1.0);
+  }
+  acc.end();
+}
+
+// Components from the multigrid hierarchy of the band solve.  A node of level l+1 is a 2x2x2
+// cell of level-l nodes, and two level-(l+1) nodes are coupled exactly when a level-l coupling
+// crosses between them.  If the children of every cell are connected inside the cell, the
+// components of each level are the components of the next coarser one, so labelling the
+// coarsest level (at most kCCCoarse nodes, one block) and following each band node's chain of
+// parents gives the band's components.  A cell whose children split inside it, or a coarsest
+// level that does not fit one block, sets the fallback flag and the union-find above runs.
+constexpr int kCCCoarse = 1024;
+constexpr int kCCMaxLev = 7;
+
+struct CCLevel {
+  const int* cnt;     // node count
+  const int* nb;      // neighbour node of each face (the node itself where there is no coupling)
+  const int* child;   // child[k * cap + I]: node of the finer level in sub-cell k, -1 if none
+  const int* agg;     // parent node on the next coarser level
+  int cap;
+};
+struct CCLevels {
+  int nlev, is3d;
+  CCLevel L[kCCMaxLev];
+};
+
+// Are the children of each cell connected inside it?  Sub-cell k = a + 2 b + 4 c (x, y, z bits);
+// its in-cell neighbour across axis d is k ^ (1 << d), reached through face 2 d (+) when bit d of
+// k is 0 and face 2 d + 1 (-) when it is 1.
+static __global__ void k_cc_check(CCLevels lv, int* fallback) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  const int nax = lv.is3d ? 3 : 2;
+  for (int l = 0; l + 1 < lv.nlev; ++l) {
+    const CCLevel& F = lv.L[l];
+    const CCLevel& Cl = lv.L[l + 1];
+    const int Mc = *Cl.cnt;
+    for (int I = tid; I < Mc; I += nth) {
+      int ch[8];
+      unsigned pres = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        ch[k] = Cl.child[k * Cl.cap + I];
+        if (ch[k] >= 0) pres |= 1u << k;
+      }
+      if (__popc(pres) <= 1) continue;
+      unsigned adj[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        adj[k] = 0;
+        if (!((pres >> k) & 1)) continue;
+        for (int d = 0; d < nax; ++d) {
+          const int k2 = k ^ (1 << d);
+          if (!((pres >> k2) & 1)) continue;
+          const int f = 2 * d + ((k >> d) & 1);
+          if (F.nb[f * F.cap + ch[k]] == ch[k2]) adj[k] |= 1u << k2;
+        }
+      }
+      unsigned r = pres & (~pres + 1u);   // lowest present sub-cell
+#pragma unroll
+      for (int it = 0; it < 3; ++it) {    // the cube graph has diameter 3
+        unsigned nr = r;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if ((r >> k) & 1) nr |= adj[k];
+        r = nr;
+      }
+      if (r != pres) atomicExch(fallback, 1);
+    }
+  }
+}
+
+// Label the coarsest level in one block: min-label propagation with pointer jumping (bounded
+// by the node count), compact ids of the roots, the component count.
+static __global__ void __launch_bounds__(kCCCoarse) k_cc_coarsest(CCLevels lv, int* __restrict__ ccL,
+                                                                  int* __restrict__ ncomp, int* fallback) {
+  __shared__ int lab[kCCCoarse];
+  __shared__ int cid[kCCCoarse];
+  __shared__ int nroot;
+  if (*(volatile int*)fallback) return;
+  const CCLevel& L = lv.L[lv.nlev - 1];
+  const int M = *L.cnt;
+  if (M > kCCCoarse) {
+    if (threadIdx.x == 0) atomicExch(fallback, 1);
+    return;
+  }
+  const int i = threadIdx.x;
+  if (i < M) lab[i] = i;
+  if (i == 0) nroot = 0;
+  __syncthreads();
+  for (int it = 0; it <= M; ++it) {
+    int m = i < M ? lab[i] : 0;
+    if (i < M) {
+      for (int f = 0; f < 6; ++f) {
+        const int j = L.nb[f * L.cap + i];
+        if (j != i) m = min(m, lab[j]);
+      }
+      m = min(m, lab[m]);
+    }
+    __syncthreads();
+    const bool ch = i < M && m < lab[i];
+    if (ch) lab[i] = m;
+    if (!__syncthreads_or(ch)) break;
+  }
+  if (i < M && lab[i] == i) cid[i] = atomicAdd(&nroot, 1);
+  __syncthreads();
+  if (i < M) ccL[i] = cid[lab[i]];
+  if (i == 0) *ncomp = nroot;
+}
+
+// Each band node's component through its chain of parents; the component sizes.
+static __global__ void k_cc_down(CCLevels lv, const int* __restrict__ ccL, const int* __restrict__ ncomp,
+                                 int* __restrict__ comp, double* __restrict__ csize, const int* fallback) {
+  __shared__ double sh[kCompShared];
+  if (*fallback) return;
+  const int M = *lv.L[0].cnt;
+  const int C = *ncomp;
+  if (C <= 1) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) csize[0] = (double)M;
+    return;
+  }
+  CompAcc acc{sh, csize, C};
+  acc.begin();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    int j = i;
+    for (int l = 0; l + 1 < lv.nlev; ++l) j = lv.L[l].agg[j];
+    const int c = ccL[j];
+    comp[i] = c;
+    acc.add(c, 1.0);
+  }
+  acc.end();
+}
+
 template <typename T>
 __device__ __forceinline__ T band_apply(const CGVec<T>& v, const T* __restrict__ a, int i) {
   const T ai = __ldcg(a + i);
@@ -870,6 +1134,10 @@ struct CGCtl {
   int maxit;
   long long budget;     // clock cycles a barrier may wait
   unsigned long long* work;  // accumulates band nodes x CG iterations (measurement)
+  const int* ncomp;     // connected band components (device)
+  const int* comp;      // component of each band node
+  const double* csize;  // nodes per component
+  double* csum;         // 2 kCompCap FP64 accumulators (zeroed before launch): f, then x
 };
 
 // Inside the band CG kernel every vector that the kernel itself writes (x, r, u, p, q and
@@ -1432,6 +1700,11 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     return;
   }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  // one band component: the plain mean; several: the mean of each (Sec. 2.1 per component)
+  const int C = c.ncomp ? *c.ncomp : 1;
+  __shared__ double csh[kCompShared];
+  CompAcc cacc{csh, c.csum, C};
+  if (C > 1) cacc.begin();
   double s = 0;
   for (int i = tid; i < M; i += nth) {
     const int p = idx[i];
@@ -1441,14 +1714,21 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     v.x[i] = x0;
     const double f = rhs(p);
     v.r1[i] = (T)f;             // f kept for the residual pass
-    s += f;
+    if (C > 1) cacc.add(c.comp[i], (double)(T)f);
+    else s += f;
   }
-  block_add(s, c.acc + A_SUMF);
+  if (C > 1) cacc.end();
+  else block_add(s, c.acc + A_SUMF);
   if (!grid_sync(c)) return;
   const double meanf = *(volatile double*)(c.acc + A_SUMF) / M;
   double bb = 0, rr = 0;
   for (int i = tid; i < M; i += nth) {
-    const double b = (double)__ldcg(v.r1 + i) - meanf;
+    double mf = meanf;
+    if (C > 1) {
+      const int ci = c.comp[i];
+      mf = __ldcg(c.csum + ci) / c.csize[ci];
+    }
+    const double b = (double)__ldcg(v.r1 + i) - mf;
     const T r = (T)(b - (double)band_apply(v, v.x, i));
     v.r[i] = r;
     bb += b * b;
@@ -1553,16 +1833,29 @@ __global__ void __launch_bounds__(1024, 1) k_cg(const int* __restrict__ idx, con
     alpha = gnew / den;
     gamma = gnew;
   }
-  // zero-mean projection of the solution (single band component)
+  // zero-mean projection of the solution (per band component)
   if (!grid_sync(c)) return;
   double sx = 0;
-  for (int i = tid; i < M; i += nth) sx += (double)__ldcg(v.x + i);
-  block_add(sx, c.acc + A_SUMX);
+  if (C > 1) {
+    cacc.dst = c.csum + kCompCap;
+    cacc.begin();
+  }
+  for (int i = tid; i < M; i += nth) {
+    if (C > 1) cacc.add(c.comp[i], (double)__ldcg(v.x + i));
+    else sx += (double)__ldcg(v.x + i);
+  }
+  if (C > 1) cacc.end();
+  else block_add(sx, c.acc + A_SUMX);
   if (!grid_sync(c)) return;
   const T mx = (T)(*(volatile double*)(c.acc + A_SUMX) / M);
   for (int i = tid; i < M; i += nth) {
     const int p = idx[i];
-    const T w = __ldcg(v.x + i) - mx;
+    T mi = mx;
+    if (C > 1) {
+      const int ci = c.comp[i];
+      mi = (T)(__ldcg(c.csum + kCompCap + ci) / c.csize[ci]);
+    }
+    const T w = __ldcg(v.x + i) - mi;
     wfull[p] = w;
     if (gs.hist) gs.hist[p] = w;
   }

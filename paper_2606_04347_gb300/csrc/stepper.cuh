@@ -12,6 +12,8 @@
 
 namespace etd {
 
+static_assert(kCCMaxLev >= kMGMax, "component labelling covers every multigrid level");
+
 // phi_0, phi_1, phi_2 of Sec. 2.2 in FP64: Taylor series below z = 1 (the closed forms
 // cancel there), closed forms through expm1 above.
 inline void phi_functions(double z, double& p0, double& p1, double& p2) {
@@ -291,6 +293,12 @@ template <typename T> class Stepper : public PlanBase {
     mc_.dim = P_.dim;
     mc_.linear_only = P_.linear_only;
 
+    // limits of the bounded device waits; ETD_WAIT_BUDGET (clock cycles a grid barrier of the
+    // band solve may wait) and ETD_WAIT_TRIES (polls of a pass-A tensor copy) lower them, so
+    // that tests can make a wait run out and check the ETD_ETIMEOUT path
+    if (const char* e = std::getenv("ETD_WAIT_BUDGET")) wait_budget_ = std::atoll(e);
+    if (const char* e = std::getenv("ETD_WAIT_TRIES")) wait_tries_ = std::atoll(e);
+
     // side stream and fork/join events of the band set-up overlap
     ETD_CUDA(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
     ETD_CUDA(cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
@@ -311,6 +319,14 @@ template <typename T> class Stepper : public PlanBase {
     cg_.nb = alloc<int>(6 * (size_t)g_.n);
     cg_.c16 = sizeof(T) == 4 ? alloc<__half>(6 * (size_t)g_.n) : nullptr;
     bmap_ = alloc<int>(g_.n);
+    cc_parent_ = alloc<int>(g_.n);
+    cc_cid_ = alloc<int>(g_.n);
+    cc_comp_ = alloc<int>(g_.n);
+    ncomp_ = alloc<int>(2);   // component count, fallback flag of the labelling
+    ETD_CUDA(cudaMemset(ncomp_, 0, 2 * sizeof(int)));
+    ccL_ = alloc<int>(kCCCoarse);
+    csize_ = alloc<double>(kCompCap);
+    csum_ = alloc<double>(2 * kCompCap);
     for (T*& h : hs_) {
       h = alloc<T>(g_.n);
       ETD_CUDA(cudaMemset(h, 0, sizeof(T) * g_.n));
@@ -499,7 +515,7 @@ template <typename T> class Stepper : public PlanBase {
     // tile, then (staged store) the leftover-column buffer after the barrier slot
     const size_t smem = tma_bar_off_ + 16 + (size_t)ETD_PASSA_THREADS * sizeof(C);
     set_smem((const void*)k, smem);
-    PassAIn pout{0, tma_box_, (int)tma_bar_off_, status_};
+    PassAIn pout{0, tma_box_, (int)tma_bar_off_, status_, wait_tries_};
     const CUtensorMap* map = tma_for(out, pout);
     timed(ETD_K_FFT_A_FWD, pro_reads(pro) * fld() + spc(), [&] {
       k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smem, st_>>>(g_, pro, out, twx_, twy_, *map, pout);
@@ -521,7 +537,7 @@ template <typename T> class Stepper : public PlanBase {
     auto k = passA_inv<T, Epi>;
     const size_t smem = tma_bar_off_ + 16;
     set_smem((const void*)k, smem);
-    PassAIn pin{0, tma_box_, (int)tma_bar_off_, status_};
+    PassAIn pin{0, tma_box_, (int)tma_bar_off_, status_, wait_tries_};
     const CUtensorMap* map = tma_for(in, pin);
     timed(ETD_K_FFT_A_INV, spc() + epi_fields(epi) * fld(), [&] {
       k<<<(g_.nz / g_.ZB) * g_.Y1, ETD_PASSA_THREADS, smem, st_>>>(g_, in, epi, twx_, twy_, *map, pin);
@@ -534,7 +550,7 @@ template <typename T> class Stepper : public PlanBase {
   template <typename Pro> void fwd_d(Pro pro, dcomplex* out) {
     auto k = passA_fwd<dfloat, Pro>;
     set_smem((const void*)k, smemAd_);
-    PassAIn p{0, 0, 0, status_};
+    PassAIn p{0, 0, 0, status_, wait_tries_};
     timed(ETD_K_FFT_A_FWD, fld() + dspc(), [&] {
       k<<<(gd_.nz / gd_.ZB) * gd_.Y1, ETD_PASSA_THREADS, smemAd_, st_>>>(gd_, pro, out, twx_d_, twy_d_, tma_none_, p);
     });
@@ -651,6 +667,7 @@ template <typename T> class Stepper : public PlanBase {
     if (s == 5) throw Error(ETD_ENOTCONV, "band CG did not reach cg_rtol within cg_maxit iterations");
     if (s == 6) throw Error(ETD_ETIMEOUT, "grid barrier of the band CG timed out");
     if (s == 7) throw Error(ETD_ETIMEOUT, "a tensor copy of the FFT pass A did not complete");
+    if (s == 8) throw Error(ETD_EINVAL, "the band has more connected components than the band solve supports (4096)");
     throw Error(ETD_ECUDA, "device status word set");
   }
 
@@ -686,7 +703,39 @@ template <typename T> class Stepper : public PlanBase {
     CGVec<T> v = cg_;
     timed(ETD_K_BAND, 0.0, [&] { k_cg_setup<T><<<nsm_ * 8, 256, 0, st_>>>(g_, mc_, idx_, count_, mask_, bmap_, G, v); });
     mg_setup();
+    label_components();
     ETD_CUDA(cudaGetLastError());
+  }
+
+  // Connected components of the band (their count, each node's component, their sizes): from
+  // the multigrid hierarchy when every aggregate is connected inside its cell, else by the
+  // union-find over the band (both enqueued; the one not needed returns at once).
+  void label_components() {
+    CGVec<T> v = cg_;
+    CCLevels lv{};
+    lv.nlev = mg_nlev_;
+    lv.is3d = g_.nz > 1;
+    for (int l = 0; l < mg_nlev_; ++l) {
+      const HostLevel& H = lv_[l];
+      CCLevel& C = lv.L[l];
+      C.cap = H.cap;
+      C.agg = H.agg;
+      C.cnt = l == 0 ? count_ : H.cnt;
+      C.nb = l == 0 ? cg_.nb : H.nb;
+      C.child = l == 0 ? nullptr : H.child;
+    }
+    timed(ETD_K_BAND, 0.0, [&] {
+      ETD_CUDA(cudaMemsetAsync(ncomp_, 0, 2 * sizeof(int), st_));   // count, fallback flag
+      ETD_CUDA(cudaMemsetAsync(csize_, 0, sizeof(double) * kCompCap, st_));
+      int* fb = ncomp_ + 1;
+      if (mg_nlev_ > 1) k_cc_check<<<nsm_ * 2, 256, 0, st_>>>(lv, fb);
+      k_cc_coarsest<<<1, kCCCoarse, 0, st_>>>(lv, ccL_, ncomp_, fb);
+      k_cc_down<<<nsm_ * 4, 256, 0, st_>>>(lv, ccL_, ncomp_, cc_comp_, csize_, fb);
+      k_cc_init<T><<<nsm_ * 4, 256, 0, st_>>>(count_, v, cc_parent_, fb);
+      k_cc_link<T><<<nsm_ * 4, 256, 0, st_>>>(count_, v, cc_parent_, status_, fb);
+      k_cc_roots<<<nsm_ * 4, 256, 0, st_>>>(count_, cc_parent_, cc_cid_, ncomp_, fb);
+      k_cc_label<<<nsm_ * 4, 256, 0, st_>>>(count_, cc_parent_, cc_cid_, ncomp_, cc_comp_, csize_, status_, fb);
+    });
   }
 
   // Initial guesses of the band solves of a step.  With P_n, C_n the predictor- and
@@ -738,8 +787,13 @@ template <typename T> class Stepper : public PlanBase {
     c.resid = cg_resid_;
     c.rtol = rtol > 0.0 ? rtol : P_.cg_rtol;
     c.maxit = P_.cg_maxit;
-    c.budget = 4000000000LL;
+    c.budget = wait_budget_;
     c.work = cg_work_;
+    c.ncomp = ncomp_;
+    c.comp = cc_comp_;
+    c.csize = csize_;
+    c.csum = csum_;
+    ETD_CUDA(cudaMemsetAsync(csum_, 0, sizeof(double) * 2 * kCompCap, st_));
     ETD_CUDA(cudaMemsetAsync(acc_, 0, sizeof(double) * 16, st_));
     ETD_CUDA(cudaMemsetAsync(bar_, 0, sizeof(unsigned) * 2, st_));
     auto k = k_cg<T, Rhs>;
@@ -1205,6 +1259,8 @@ template <typename T> class Stepper : public PlanBase {
   T c_lap_{};
   double hvol_ = 1.0;
   int nsm_ = 1;
+  long long wait_budget_ = 4000000000LL;   // grid barrier: clock cycles before ETD_ETIMEOUT
+  long long wait_tries_ = 1LL << 22;       // pass-A tensor copy: mbarrier polls before ETD_ETIMEOUT
   size_t smemA_ = 0, smemB1_ = 0;
   std::vector<void*> allocs_;
   C* I_[5] = {};
@@ -1220,6 +1276,9 @@ template <typename T> class Stepper : public PlanBase {
   CGVec<T> cg_{};
   unsigned char* mask_ = nullptr;
   int* bmap_ = nullptr;
+  // connected components of the band: union-find parents, root ids, node components, sizes
+  int *cc_parent_ = nullptr, *cc_cid_ = nullptr, *cc_comp_ = nullptr, *ncomp_ = nullptr, *ccL_ = nullptr;
+  double *csize_ = nullptr, *csum_ = nullptr;
   // multigrid hierarchy of the band solve (level 0 = the band itself)
   struct HostLevel {
     int lx = 0, ly = 0, lz = 0, cap = 0, nblk = 0;

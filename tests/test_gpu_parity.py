@@ -186,6 +186,67 @@ def test_fixed_3d_matches_oracle(scheme):
     assert rel_l2(host(ud), want) < 1e-11
 
 
+def _two_spheres(n):
+    """c3 coupled parameters on a membrane of two separated spheres: a two-component band."""
+    p = wl.workload("c3", n=n)[0]
+    phi = wl.two_spheres_phi(p, (0.8, 0.6), ((-1.6, 0.0, 0.0), (1.6, 0.0, 0.0)), 0.12)
+    band = obm.band_mask(phi, p.band_mask_hi)
+    assert obm.components(band)[1] == 2
+    u = np.where(band, wl.random_fields(p.shape, 7, 0.45, 0.55), 0.5)
+    return p, phi, u, band
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_nonlocal_two_component_band_matches_oracle(n):
+    """Sec. 2.1 mean removal per connected band component: each component's solution has zero
+    mean and the whole solution matches the oracle's per-component solve."""
+    p, phi, u, band = _two_spheres(n)
+    p = p.replace(cg_rtol=1e-13)
+    g = omodel.g_loc(phi)
+    f = np.where(band, wl.random_fields(p.shape, 8, -1.0, 1.0), 0.0)
+    want, _, _ = obm.solve_neg_lap(f, g, band, p.h, rtol=1e-14)
+    plan = Plan(p)
+    w = torch.zeros(p.shape, dtype=torch.float64, device=DEV)
+    it, rs = plan.nonlocal_solve(dev(phi, 0), dev(f, 0), w)
+    got = host(w)
+    comp, nc = obm.components(band)
+    for c in range(nc):
+        assert abs(got[comp == c].mean()) < 1e-12 * np.abs(got).max()
+    assert rs <= 1e-13
+    assert rel_l2(got, want) < 1e-10
+
+
+def test_nonlocal_many_columns_band_matches_oracle():
+    """A band of 128 disconnected z-columns (x + y even on a 16^3 grid): the cells of the
+    multigrid hierarchy hold columns that touch only diagonally, so the labelling falls back to
+    the union-find over the band, and the many components take the per-warp sums."""
+    p = wl.workload("c3", n=16)[0].replace(cg_rtol=1e-13)
+    z, y, x = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
+    phi = np.where((x + y) % 2 == 0, 0.5, 0.0)
+    band = obm.band_mask(phi, p.band_mask_hi)
+    assert obm.components(band)[1] == 128
+    g = omodel.g_loc(phi)
+    f = np.where(band, wl.random_fields(p.shape, 9, -1.0, 1.0), 0.0)
+    want, _, _ = obm.solve_neg_lap(f, g, band, p.h, rtol=1e-14)
+    plan = Plan(p)
+    w = torch.zeros(p.shape, dtype=torch.float64, device=DEV)
+    it, rs = plan.nonlocal_solve(dev(phi, 0), dev(f, 0), w)
+    assert rs <= 1e-13
+    assert rel_l2(host(w), want) < 1e-10
+
+
+def test_coupled_two_component_band_matches_oracle_fp64():
+    p, phi, u, _ = _two_spheres(32)
+    cs = oetd.CoupledStepper(p)
+    wphi, wu = cs.run(phi.copy(), u.copy(), 2)
+    plan = Plan(p)
+    phid, ud = dev(phi, 0), dev(u, 0)
+    d = plan.step(phid, ud, 2, diag=True)
+    assert rel_l2(host(phid), wphi) < 1e-11
+    assert rel_l2(host(ud), wu) < 1e-11
+    assert d["cg_resid_last"] <= p.cg_rtol
+
+
 @pytest.mark.parametrize("scheme,n,steps", [(2, 32, 4), (1, 32, 4), (2, 64, 2)])
 def test_coupled_matches_oracle_fp64(scheme, n, steps):
     p, phi, u, _ = wl.workload("c3", n=n, scheme=scheme)
