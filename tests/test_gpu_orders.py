@@ -47,3 +47,32 @@ def test_fixed_scheme_orders_on_gpu():
     print("fixed 32^2 rates on the GPU: ETD1", rates[1], "ETDRK2", rates[2])
     assert 0.85 <= rates[1][-1] <= 1.15
     assert 1.75 <= rates[2][-1] <= 2.25
+
+
+def test_c2_128_etdrk2_order_fp64_and_fp32():
+    """The 128^3 fixed-membrane ETDRK2 sweep of the c2 configuration, FP64 and FP32-mixed side
+    by side against one FP64 fine-step solution (tau/256, T = 0.04).  The configuration's own
+    steps (1e-2 ... 1.25e-3) are before the asymptotic range at this resolution (errors of
+    order one, in both precisions alike), so the sweep runs 2 to 16 times finer, where the
+    relative L2 error on the membrane core {G > 0.1} shows the second order and the FP32 form
+    has the FP64 form's errors."""
+    p, phi, u0, _ = wl.workload("c2", n=128)
+    T = 0.04
+    core = omodel.g_loc(phi) > 0.1
+
+    def run(tau, prec):
+        dt = torch.float64 if prec == 0 else torch.float32
+        plan = Plan(p.replace(tau=tau, precision=prec, cg_rtol=1e-12 if prec == 0 else 1e-6))
+        u = torch.tensor(u0, dtype=dt, device=DEV)
+        plan.step(torch.tensor(phi, dtype=dt, device=DEV), u, int(round(T / tau)))
+        return u.cpu().numpy().astype(np.float64)
+
+    ref = run(1.25e-3 / 256, 0)
+    errs = {}
+    for prec in (0, 1):
+        errs[prec] = [np.linalg.norm((run(1.25e-3 / m, prec) - ref)[core]) / np.linalg.norm(ref[core])
+                      for m in (2, 4, 8, 16)]
+    r64, r32 = _rates(errs[0]), _rates(errs[1])
+    print("c2 128^3 ETDRK2 core errors fp64", errs[0], "rates", r64, "fp32 rates", r32)
+    assert r64[-1] >= 1.7 and r32[-1] >= 1.7
+    assert all(abs(a - b) <= 1e-3 * b for a, b in zip(errs[1], errs[0]))
