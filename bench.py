@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=64, help="grid of the oracle sample")
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=19, help="steps of the FP64 comparison leg (0: skip)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
     return ap.parse_args()
 
 
@@ -234,6 +235,80 @@ def run_reference(a):
     return 0
 
 
+def batch_leg(stream, peak):
+    """The batched fixed-membrane sweep: 48 runs (64^3 / 96^3 / 128^3, seeds 100-147), FP32-mixed
+    ETDRK2, 200 steps each, tiles autotuned per grid, 6-step blocks replayed as one CUDA graph.
+    Timed: steps 3-200 of every run (the first two run eagerly, then the graph is recorded and
+    replayed 33 times).  Bytes: each run's algorithmic bytes per step, from one single-plan
+    replay of the same steps with per-launch counters; the same single plans, one run at a
+    time with default tiles and no graph, give the comparison time."""
+    import torch
+    from paper_2606_04347_gb300 import Batch, Plan
+    from paper_2606_04347_gb300 import workloads as wl
+    runs = []
+    for seed in range(100, 148):
+        p, phi, u, nsteps = wl.c4_run(seed, 1)
+        runs.append((p.replace(cg_rtol=1e-5), phi, u))
+    t0 = time.perf_counter()
+    b = Batch([r[0] for r in runs], stream=stream, autotune=True)
+    t_plan = time.perf_counter() - t0
+    phis = [torch.tensor(r[1], dtype=torch.float32, device="cuda") for r in runs]
+    us = [torch.tensor(r[2], dtype=torch.float32, device="cuda") for r in runs]
+    b.step(phis, us, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(None, us, 198)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    from paper_2606_04347_gb300.abi import EtdError
+    try:
+        diag, check = b.check(None, us), "ok"
+    except EtdError as ex:
+        diag, check = [], str(ex)
+    tiles = {}
+    for i, r in enumerate(runs):
+        tiles.setdefault(r[0].n[0], b.info(i))
+    graph = b.info(0)["graph"]
+    b.close()
+    del phis, us
+    pts = sum(r[0].n[0] ** 3 for r in runs)
+    # one run at a time (default tiles, eager), with the per-launch counters for the bytes
+    t_single, nbytes = 0.0, 0.0
+    for p, phi, u in runs:
+        plan = Plan(p, stream=stream)
+        f = torch.tensor(phi, dtype=torch.float32, device="cuda")
+        ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+        plan.step(f, ud, 2)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        plan.step(None, ud, 198)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t_single += f0.elapsed_time(f1)
+        plan.timing(True)
+        plan.step(None, ud, 6)
+        nbytes += sum(v[2] for v in plan.timing_read().values()) / 6 * 198
+        plan.timing(False)
+        plan.close()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    finite = check == "ok" and all(d["band_size"] > 0 for d in diag)
+    return {
+        "workload": "c4: 48 fixed-membrane OK runs, grids 64^3/96^3/128^3 (16/21/11), eps in [0.03,0.08], "
+                    "sigma in [10,200], S in {1,2,4}, tau in {1e-3,2e-3,5e-3}, seeds 100-147, ETDRK2 FP32, 200 steps",
+        "value": pts * 198 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_steps_3_to_200": ms, "graph": graph,
+        "tiles_by_grid": {str(k): {kk: vv for kk, vv in v.items() if kk != "graph"} for k, v in tiles.items()},
+        "autotune_and_plans_s": round(t_plan, 2),
+        "one_run_at_a_time": {"value": pts * 198 / (t_single / 1e3) / 1e6, "ms": t_single},
+        "speedup_over_one_at_a_time": t_single / ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "bytes_per_step": nbytes / 198},
+        "all_runs_finite": finite, "check": check,
+    }
+
+
 def run_ours(a):
     import torch
     rank, world, local = dist_env()
@@ -345,6 +420,10 @@ def run_ours(a):
                 "max_bound_fp32": d32["max_bound"], "max_bound_fp64": d64["max_bound"]}
         plan64.close()
 
+    batch = None
+    if not a.no_batch and rank == 0 and prec == 1:
+        batch = batch_leg(stream, peak)
+
     # end to end through the public API with host buffers
     esize = 4 if prec else 8
     h_phi = torch.from_numpy(phi0.astype(np.float32 if prec else np.float64)).pin_memory()
@@ -391,6 +470,7 @@ def run_ours(a):
                               "bytes_per_point_step": step_bytes / a.steps / npts, "achieved": step_achieved,
                               "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
             "fp64_gpu": fp64,
+            "batch_c4": batch,
             "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
             "kernel_ms_steps": a.steps, "timed_with_events_ms_per_step": ms_t / a.steps,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * npts * esize,

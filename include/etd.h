@@ -20,8 +20,10 @@
  *    in etd_free.  A plan is not thread-safe; use one plan per host thread.
  *  - No C++ exception crosses this boundary.  Errors come back as etd_status; the
  *    message of the last error of the calling thread is returned by etd_last_error().
- *  - Supported grids: every N a power of two, 8 <= N <= 256 along x and y, N_z in
- *    {1 (2D)} or 8..256, cubic boxes X = Y (= Z).  Other sizes return ETD_EINVAL.
+ *  - Supported grids: every N a power of two from 8 to 256, or 96, along x and y; N_z = 1
+ *    (2D) or one of the same lengths; cubic boxes X = Y (= Z).  The FP32-mixed coupled form
+ *    needs powers of two.  Other sizes return ETD_EINVAL.  (etd_fft_forward_noalloc: powers
+ *    of two only.)
  */
 #ifndef ETD_H
 #define ETD_H
@@ -154,6 +156,43 @@ etd_status etd_nonlocal(etd_plan_t plan, const void *phi, const void *f, void *w
  * Synchronous. */
 etd_status etd_remainder(etd_plan_t plan, int which, const void *phi, const void *phi_old,
                          const void *u, void *out);
+
+/* ---- Batched runs (many independent simulations, Sec. 2 fixed model or Sec. 3 coupled) -- */
+
+typedef struct etd_batch_s *etd_batch_t;
+
+/* Create a batch of `nruns` independent runs, params[i] describing run i (grids, precision,
+ * model, scheme, tau and coefficients may all differ).  Each run gets its own plan (workspace
+ * as etd_plan) and its own CUDA stream, forked from and joined back into `cuda_stream`.
+ * autotune_tiles = 1: for every distinct grid and precision, time a forward + inverse
+ * transform pair for each candidate tiling (pass-A z-planes per block, pass-B pencil blocks
+ * per block, tensor-copy staging of pass A on or off) and give the runs of that grid the
+ * fastest; 0: default tiles.  Tiling never changes the results (the same arithmetic per
+ * element).  Synchronous; ETD_EINVAL names the first invalid run. */
+etd_status etd_plan_batch(const etd_params *params, int nruns, void *cuda_stream, int autotune_tiles,
+                          etd_batch_t *out);
+
+/* Advance every run `nsteps` steps in place (as etd_step on each run).  phi[i], u[i] are run
+ * i's device fields; phi is read on the first call (it fixes the membrane of fixed-model runs,
+ * which may pass NULL afterwards) and on every call of coupled runs.  The first two steps of a
+ * batch run eagerly; after that, blocks of 6 steps of all runs are recorded once into a CUDA
+ * graph (the runs as parallel branches) and replayed, the rest eagerly.  A graph is tied to
+ * the field pointers it was recorded with: other pointers re-record it.  If the graph cannot
+ * be recorded (etd_batch_info reports graph = 0), every step runs eagerly.  Asynchronous on
+ * the batch stream; errors inside the steps surface in etd_batch_check. */
+etd_status etd_batch_step(etd_batch_t batch, void *const *phi, void *const *u, int nsteps);
+
+/* Synchronise and check every run (non-finite state, band-solve convergence, device waits);
+ * fills diag[i] (nullable) as etd_step's `last`.  Returns the first run's error. */
+etd_status etd_batch_check(etd_batch_t batch, void *const *phi, void *const *u, etd_diag *diag);
+
+/* Tiles run `run` uses (pass-A z-planes, pass-B pencil blocks, tensor-copy staging 1/0) and the
+ * batch's graph state (1 replaying, 0 eager, -1 not yet recorded).  Any pointer may be NULL.
+ * When the graph could not be recorded, etd_last_error() then gives the reason. */
+etd_status etd_batch_info(etd_batch_t batch, int run, int *zb, int *kb, int *tma, int *graph);
+
+/* Release the batch (synchronises its stream).  etd_batch_free(NULL) returns ETD_OK. */
+etd_status etd_batch_free(etd_batch_t batch);
 
 /* ---- Per-kernel timing (measurement support; no counterpart in the paper) ----------- */
 

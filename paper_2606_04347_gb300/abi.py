@@ -70,6 +70,16 @@ SIGNATURES = {
                                    ct.POINTER(ct.c_double)]),
 }
 
+SIGNATURES.update({
+    "etd_plan_batch": (ct.c_int, [ct.POINTER(etd_params), ct.c_int, ct.c_void_p, ct.c_int, ct.POINTER(ct.c_void_p)]),
+    "etd_batch_step": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_void_p), ct.c_int]),
+    "etd_batch_check": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_void_p),
+                                   ct.POINTER(etd_diag)]),
+    "etd_batch_info": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                  ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "etd_batch_free": (ct.c_int, [ct.c_void_p]),
+})
+
 SIGNATURES["etd_fft_forward_noalloc"] = (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.c_int, ct.c_void_p,
                                                   ct.c_void_p, ct.c_void_p])
 
@@ -198,3 +208,54 @@ class Plan:
                                       _ptr(u, self.dtype), _ptr(out, self.dtype)))
 
 
+
+
+class Batch:
+    """Owns one etd_batch_t: independent runs, each with its own plan and stream."""
+
+    def __init__(self, params_list, stream=None, autotune=True):
+        import torch
+        self.lib = load_library()
+        self.params = list(params_list)
+        n = len(self.params)
+        self._arr = (etd_params * n)(*[params_struct(p) for p in self.params])
+        self.dtypes = [torch.float64 if p.precision == 0 else torch.float32 for p in self.params]
+        h = ct.c_void_p()
+        st = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+        _check(self.lib.etd_plan_batch(self._arr, n, st, 1 if autotune else 0, ct.byref(h)))
+        self.h = h
+
+    def _ptrs(self, tensors):
+        n = len(self.params)
+        if tensors is None:
+            return None
+        vals = [None if t is None else _ptr(t, self.dtypes[i]) for i, t in enumerate(tensors)]
+        return (ct.c_void_p * n)(*vals)
+
+    def step(self, phis, us, nsteps):
+        _check(self.lib.etd_batch_step(self.h, self._ptrs(phis), self._ptrs(us), int(nsteps)))
+
+    def check(self, phis, us):
+        n = len(self.params)
+        d = (etd_diag * n)()
+        _check(self.lib.etd_batch_check(self.h, self._ptrs(phis), self._ptrs(us), d))
+        return [d[i].as_dict() for i in range(n)]
+
+    def info(self, run):
+        zb, kb, tma, graph = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+        _check(self.lib.etd_batch_info(self.h, int(run), ct.byref(zb), ct.byref(kb), ct.byref(tma), ct.byref(graph)))
+        out = {"zb": zb.value, "kb": kb.value, "tma": tma.value, "graph": graph.value}
+        if graph.value == 0:
+            out["graph_error"] = self.lib.etd_last_error().decode()
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.etd_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -63,6 +63,7 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 struct Geo {
   int dim, nx, ny, nz, nxh;
   int lx, ly;          // log2 nx, log2 ny (neighbour arithmetic of the pointwise kernels)
+  int pow2;            // every extent a power of two (shift-and-mask neighbours)
   int Y1, Y2, ZB, KB;
   long long n, nhat;
   double hx, hy, hz;
@@ -89,10 +90,19 @@ struct Geo {
 // Shared-memory padding: one spare slot every 16 complex elements (bank spreading).
 __host__ __device__ __forceinline__ int pad16(int k) { return k + (k >> 4); }
 
-// R and S of the team transform of an axis of length n (a power of two up to 256): S lanes
-// with R = min(n, 16) values each.
-__host__ __device__ __forceinline__ constexpr int team_R(int n) { return n < 16 ? n : 16; }
+// R and S of the team transform of an axis of length n: S lanes (a power of two) with R values
+// each, R a multiple of S (the second stage runs R/S transforms of length S per lane).  Powers
+// of two up to 256: R = min(n, 16); 96 = 24 x 4.
+__host__ __device__ __forceinline__ constexpr int team_R(int n) { return n == 96 ? 24 : (n < 16 ? n : 16); }
 __host__ __device__ __forceinline__ constexpr int team_S(int n) { return n / team_R(n); }
+// Axis lengths the two-pass transform supports.
+__host__ __device__ __forceinline__ constexpr bool fft_length_ok(int n) {
+  return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 96;
+}
+// The long axis (x in pass A, z in pass B) of a launch: a power of two (family 0) or 96
+// (family 1); each family is its own kernel instantiation, so the 24-value registers of the
+// 96-point team never weigh on the power-of-two kernels.
+__host__ __device__ __forceinline__ constexpr int fft_family(int n) { return n == 96 ? 1 : 0; }
 
 // Tile row pitches.  A team's exchange scratch (S (R + 1) values) lives in the rows it works
 // on: a pair of pass-A rows, one pass-B row.
@@ -108,21 +118,36 @@ __host__ __device__ __forceinline__ int pitch_b(int nz) {
 
 // Tile choice shared by the plan and the allocation-free entry point.  Returns false if the
 // grid is not supported.  smemA: pass-A tile; smemB1: one pass-B operand tile.
-inline bool choose_tiles(Geo& g, size_t csize, size_t& smemA, size_t& smemB1) {
+//   pass A: ZB z-planes x Y2 rows per CTA; zb_req > 0 asks for ZB (a divisor of Nz), else
+//           4 (8-byte complex) or 2 (16-byte complex);
+//   pass B: KB consecutive kx pencil blocks of Y1 x Nz per CTA.  A team of S lanes takes one
+//           row (two in 2D), so KB Y1 is at most the block's rows; kb_req > 0 asks for KB, else
+//           1 in 3D (the most CTAs) and as many as the block holds in 2D.
+inline int passb_max_rows(int nz) {
+  const int rpt = team_R(nz) >= 8 ? 1 : 2;
+  return (ETD_PASSB_THREADS / team_S(nz)) * rpt;
+}
+inline bool choose_tiles(Geo& g, size_t csize, size_t& smemA, size_t& smemB1, int zb_req = 0, int kb_req = 0) {
+  if (!fft_length_ok(g.nx) || !fft_length_ok(g.ny) || !(g.nz == 1 || fft_length_ok(g.nz))) return false;
   g.Y2 = g.ny < 16 ? g.ny : 16;
   g.Y1 = g.ny / g.Y2;
   if (g.Y1 > 16 || g.Y2 < 2) return false;
-  const int zb = csize == 8 ? ETD_ZB32 : (ETD_ZB32 > 1 ? ETD_ZB32 / 2 : 1);
+  const int zb = zb_req > 0 ? zb_req : (csize == 8 ? ETD_ZB32 : (ETD_ZB32 > 1 ? ETD_ZB32 / 2 : 1));
   g.ZB = g.nz == 1 ? 1 : (g.nz < zb ? g.nz : zb);
+  if (g.nz % g.ZB) return false;
   const int rsa = pitch_a(g.nx);
   smemA = (size_t)g.ZB * g.Y2 * rsa * csize;
-  if (g.nz > 1) {
+  const int rsb = pitch_b(g.nz);
+  const int kbmax = passb_max_rows(g.nz) / g.Y1;
+  if (kb_req > 0) {
+    g.KB = kb_req;
+  } else if (g.nz > 1) {
     g.KB = 1;
   } else {
     g.KB = 512 / g.Y1;
-    if (g.KB > g.nxh) g.KB = g.nxh;
   }
-  const int rsb = pitch_b(g.nz);
+  if (g.KB > g.nxh) g.KB = g.nxh;
+  if (g.KB < 1 || g.KB > kbmax) return false;
   smemB1 = (size_t)g.KB * g.Y1 * rsb * csize;
   return smemA <= 200 * 1024 && 2 * smemB1 <= 200 * 1024;
 }
@@ -172,13 +197,6 @@ template <typename C, bool INV> __device__ __forceinline__ void dft8(C* v) {
   }
 }
 
-template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C* v) {
-  if (R == 2) dft2<C, INV>(v);
-  else if (R == 4) dft4<C, INV>(v);
-  else dft8<C, INV>(v);
-}
-
-
 // 16-point DFT as 4 x 4 (inner DFT4 over n2 for each n1, twiddle w16^(n1 k1), outer DFT4).
 template <typename C, bool INV> __device__ __forceinline__ void dft16(C* v) {
   using T = decltype(v[0].x);
@@ -205,12 +223,85 @@ template <typename C, bool INV> __device__ __forceinline__ void dft16(C* v) {
   }
 }
 
-// Natural-order DFT of compile-time length N in registers (N = 1, 2, 4, 8, 16).
+// 3-point DFT: X0 = a + b + c, X1,2 = a - (b + c)/2 -/+ i (sqrt(3)/2)(b - c) (forward).
+template <typename C, bool INV> __device__ __forceinline__ void dft3(C* v) {
+  using T = decltype(v[0].x);
+  const T h = (T)0.5, s3 = (T)0.86602540378443864676;
+  const C t1 = cadd(v[1], v[2]);
+  const C t2 = C{v[0].x - h * t1.x, v[0].y - h * t1.y};
+  const C d = csub(v[1], v[2]);
+  const C sd = C{s3 * d.x, s3 * d.y};
+  v[0] = cadd(v[0], t1);
+  if (INV) {
+    v[1] = C{t2.x - sd.y, t2.y + sd.x};
+    v[2] = C{t2.x + sd.y, t2.y - sd.x};
+  } else {
+    v[1] = C{t2.x + sd.y, t2.y - sd.x};
+    v[2] = C{t2.x - sd.y, t2.y + sd.x};
+  }
+}
+
+template <typename C, int N, bool INV> __device__ __forceinline__ void dftN(C* v);
+
+// N = N1 N2 point DFT by one split: Y[n1][k2] = DFT_N2 over n2 of v[n1 + N1 n2], times
+// w_N^(n1 k2), then the N1-point DFT over n1 gives X[k2 + N2 k1].  w[m] = w_N^m.
+template <typename C, int N1, int N2, bool INV, int NW>
+__device__ __forceinline__ void dft_split(C* v, const C (&w)[NW]) {
+  C a[N1][N2];
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1) {
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) a[n1][n2] = v[n1 + N1 * n2];
+    dftN<C, N2, INV>(a[n1]);
+  }
+#pragma unroll
+  for (int n1 = 1; n1 < N1; ++n1)
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) a[n1][k2] = INV ? cmulc(a[n1][k2], w[n1 * k2]) : cmul(a[n1][k2], w[n1 * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    C b[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) b[n1] = a[n1][k2];
+    dftN<C, N1, INV>(b);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k2 + N2 * k1] = b[k1];
+  }
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft6(C* v) {
+  using T = decltype(v[0].x);
+  const C w[3] = {C{(T)1.0, (T)0.0}, C{(T)0.5, (T)-0.86602540378443864676}, C{(T)-0.5, (T)-0.86602540378443864676}};
+  dft_split<C, 2, 3, INV>(v, w);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft12(C* v) {
+  using T = decltype(v[0].x);
+  const T c = (T)0.86602540378443864676, h = (T)0.5;
+  const C w[7] = {C{(T)1.0, (T)0.0}, C{c, -h}, C{h, -c}, C{(T)0.0, (T)-1.0}, C{-h, -c}, C{-c, -h}, C{(T)-1.0, (T)0.0}};
+  dft_split<C, 4, 3, INV>(v, w);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft24(C* v) {
+  using T = decltype(v[0].x);
+  const T a = (T)0.96592582628906828675, b = (T)0.25881904510252076235, c = (T)0.86602540378443864676,
+          h = (T)0.5, r = (T)0.70710678118654752440;
+  // w_24^m, m = 0..14
+  const C w[15] = {C{(T)1.0, (T)0.0}, C{a, -b}, C{c, -h}, C{r, -r}, C{h, -c}, C{b, -a}, C{(T)0.0, (T)-1.0},
+                   C{-b, -a}, C{-h, -c}, C{-r, -r}, C{-c, -h}, C{-a, -b}, C{(T)-1.0, (T)0.0}, C{-a, b}, C{-c, h}};
+  dft_split<C, 8, 3, INV>(v, w);
+}
+
+// Natural-order DFT of compile-time length N in registers (N = 1, 2, 3, 4, 6, 8, 12, 16, 24).
 template <typename C, int N, bool INV> __device__ __forceinline__ void dftN(C* v) {
-  if (N == 2) dft2<C, INV>(v);
-  else if (N == 4) dft4<C, INV>(v);
-  else if (N == 8) dft8<C, INV>(v);
-  else if (N == 16) dft16<C, INV>(v);
+  if constexpr (N == 2) dft2<C, INV>(v);
+  else if constexpr (N == 3) dft3<C, INV>(v);
+  else if constexpr (N == 4) dft4<C, INV>(v);
+  else if constexpr (N == 6) dft6<C, INV>(v);
+  else if constexpr (N == 8) dft8<C, INV>(v);
+  else if constexpr (N == 12) dft12<C, INV>(v);
+  else if constexpr (N == 16) dft16<C, INV>(v);
+  else if constexpr (N == 24) dft24<C, INV>(v);
 }
 
 
@@ -468,7 +559,7 @@ __device__ __forceinline__ void passA_cols_fwd_staged(const Geo& g, typename Cpl
   }
 }
 
-template <typename T, typename Pro>
+template <typename T, typename Pro, int FAM = 0>
 __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_fwd(Geo g, Pro pro, typename Cplx<T>::type* __restrict__ out,
                                                  const typename Cplx<T>::type* __restrict__ twx,
                                                  const typename Cplx<T>::type* __restrict__ twy,
@@ -479,13 +570,17 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
   const int rs = pitch_a(g.nx);
   const int zb = blockIdx.x / g.Y1, n1 = blockIdx.x % g.Y1;
   const int z0 = zb * g.ZB;
-  switch (g.nx) {
-    case 8: passA_rows_fwd<T, Pro, 8, 1>(g, pro, tile, rs, z0, n1, twx); break;
-    case 16: passA_rows_fwd<T, Pro, 16, 1>(g, pro, tile, rs, z0, n1, twx); break;
-    case 32: passA_rows_fwd<T, Pro, 16, 2>(g, pro, tile, rs, z0, n1, twx); break;
-    case 64: passA_rows_fwd<T, Pro, 16, 4>(g, pro, tile, rs, z0, n1, twx); break;
-    case 128: passA_rows_fwd<T, Pro, 16, 8>(g, pro, tile, rs, z0, n1, twx); break;
-    default: passA_rows_fwd<T, Pro, 16, 16>(g, pro, tile, rs, z0, n1, twx); break;
+  if constexpr (FAM == 1) {
+    passA_rows_fwd<T, Pro, 24, 4>(g, pro, tile, rs, z0, n1, twx);
+  } else {
+    switch (g.nx) {
+      case 8: passA_rows_fwd<T, Pro, 8, 1>(g, pro, tile, rs, z0, n1, twx); break;
+      case 16: passA_rows_fwd<T, Pro, 16, 1>(g, pro, tile, rs, z0, n1, twx); break;
+      case 32: passA_rows_fwd<T, Pro, 16, 2>(g, pro, tile, rs, z0, n1, twx); break;
+      case 64: passA_rows_fwd<T, Pro, 16, 4>(g, pro, tile, rs, z0, n1, twx); break;
+      case 128: passA_rows_fwd<T, Pro, 16, 8>(g, pro, tile, rs, z0, n1, twx); break;
+      default: passA_rows_fwd<T, Pro, 16, 16>(g, pro, tile, rs, z0, n1, twx); break;
+    }
   }
   __syncthreads();
   if (st.tma && (smem_u32(tile) & 127u) == 0) {
@@ -639,7 +734,7 @@ __device__ __forceinline__ void passA_rows_inv(const Geo& g, const Epi& epi, typ
   }
 }
 
-template <typename T, typename Epi>
+template <typename T, typename Epi, int FAM = 0>
 __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_MINB : 1) passA_inv(Geo g, const typename Cplx<T>::type* __restrict__ in, Epi epi,
                                                  const typename Cplx<T>::type* __restrict__ twx,
                                                  const typename Cplx<T>::type* __restrict__ twy,
@@ -685,13 +780,17 @@ __global__ void __launch_bounds__(ETD_PASSA_THREADS, sizeof(T) == 4 ? ETD_PASSA_
   }
   __syncthreads();
   typename Epi::Acc acc{};
-  switch (g.nx) {
-    case 8: passA_rows_inv<T, Epi, 8, 1>(g, epi, tile, rs, z0, n1, twx, acc); break;
-    case 16: passA_rows_inv<T, Epi, 16, 1>(g, epi, tile, rs, z0, n1, twx, acc); break;
-    case 32: passA_rows_inv<T, Epi, 16, 2>(g, epi, tile, rs, z0, n1, twx, acc); break;
-    case 64: passA_rows_inv<T, Epi, 16, 4>(g, epi, tile, rs, z0, n1, twx, acc); break;
-    case 128: passA_rows_inv<T, Epi, 16, 8>(g, epi, tile, rs, z0, n1, twx, acc); break;
-    default: passA_rows_inv<T, Epi, 16, 16>(g, epi, tile, rs, z0, n1, twx, acc); break;
+  if constexpr (FAM == 1) {
+    passA_rows_inv<T, Epi, 24, 4>(g, epi, tile, rs, z0, n1, twx, acc);
+  } else {
+    switch (g.nx) {
+      case 8: passA_rows_inv<T, Epi, 8, 1>(g, epi, tile, rs, z0, n1, twx, acc); break;
+      case 16: passA_rows_inv<T, Epi, 16, 1>(g, epi, tile, rs, z0, n1, twx, acc); break;
+      case 32: passA_rows_inv<T, Epi, 16, 2>(g, epi, tile, rs, z0, n1, twx, acc); break;
+      case 64: passA_rows_inv<T, Epi, 16, 4>(g, epi, tile, rs, z0, n1, twx, acc); break;
+      case 128: passA_rows_inv<T, Epi, 16, 8>(g, epi, tile, rs, z0, n1, twx, acc); break;
+      default: passA_rows_inv<T, Epi, 16, 16>(g, epi, tile, rs, z0, n1, twx, acc); break;
+    }
   }
   epi.finish(acc);
 }
@@ -760,6 +859,7 @@ __device__ __forceinline__ void passB_cols_any(const Geo& g, int kbn, const type
     case 2: passB_cols<T, 2, INV>(g, kbn, src, cb, tile, rs, dst); break;
     case 4: passB_cols<T, 4, INV>(g, kbn, src, cb, tile, rs, dst); break;
     case 8: passB_cols<T, 8, INV>(g, kbn, src, cb, tile, rs, dst); break;
+    case 6: passB_cols<T, 6, INV>(g, kbn, src, cb, tile, rs, dst); break;
     default: passB_cols<T, 16, INV>(g, kbn, src, cb, tile, rs, dst); break;
   }
 }
@@ -842,7 +942,7 @@ __device__ __forceinline__ void passB_rows(const Geo& g, const Op& op, int kx0, 
   }
 }
 
-template <typename T, typename Op>
+template <typename T, typename Op, int FAM = 0>
 __global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_MINB : 1) passB(Geo g, Op op, const typename Cplx<T>::type* __restrict__ in0,
                                              const typename Cplx<T>::type* __restrict__ in1,
                                              OutP<typename Cplx<T>::type> outs,
@@ -872,6 +972,10 @@ __global__ void __launch_bounds__(ETD_PASSB_THREADS, sizeof(T) == 4 ? ETD_PASSB_
     if (Op::NI >= 2) passB_cols_any<T, false>(g, kbn, in1, cb, tile1, rs, nullptr);
   }
   __syncthreads();
+  if constexpr (FAM == 1) {
+    passB_rows<T, Op, 24, 4>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz);
+    return;
+  }
   switch (g.nz) {
     case 1: passB_rows<T, Op, 1, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;
     case 8: passB_rows<T, Op, 8, 1>(g, op, kx0, k2, kbn, cb, tile0, tile1, rs, outs, twz); break;

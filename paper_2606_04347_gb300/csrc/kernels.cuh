@@ -71,11 +71,26 @@ __device__ __forceinline__ void atomic_max_d(double* dst, double v) {
   } while (assumed != old);
 }
 
-// Periodic neighbours of flat index p (power-of-two extents: shifts and masks only).
+// Periodic neighbours of flat index p: shifts and masks when every extent is a power of two,
+// integer division otherwise.
 struct Nb {
   int c, xm, xp, ym, yp, zm, zp;
 };
 __device__ __forceinline__ Nb neighbours(const Geo& g, int p) {
+  if (!g.pow2) {
+    const int x = p % g.nx, t = p / g.nx, y = t % g.ny, z = t / g.ny;
+    const int sxy = g.nx * g.ny;
+    const int rowbase = p - x, planebase = z * sxy, inplane = p - planebase;
+    Nb n;
+    n.c = p;
+    n.xm = rowbase + (x == 0 ? g.nx - 1 : x - 1);
+    n.xp = rowbase + (x == g.nx - 1 ? 0 : x + 1);
+    n.ym = planebase + (y == 0 ? g.ny - 1 : y - 1) * g.nx + x;
+    n.yp = planebase + (y == g.ny - 1 ? 0 : y + 1) * g.nx + x;
+    n.zm = (z == 0 ? g.nz - 1 : z - 1) * sxy + inplane;
+    n.zp = (z == g.nz - 1 ? 0 : z + 1) * sxy + inplane;
+    return n;
+  }
   const int mx = g.nx - 1, my = g.ny - 1, mz = g.nz - 1;
   const int sp = g.lx + g.ly;
   const int x = p & mx;
@@ -1230,41 +1245,41 @@ template <typename T> struct MGP {
 // Multigrid set-up steps, written for any grid-stride partition (t0, ns) so that the large
 // levels run them as grid-wide kernels and the small ones all inside one block.
 
-// mark the cells of level l (grid lxc, lyc) holding nodes of level l-1 (grid lxf, lyf)
-__device__ __forceinline__ void mg_mark_body(const int* __restrict__ list, int M, int lxf, int lyf, int is3d,
-                                             int lxc, int lyc, unsigned char* __restrict__ mark, int t0, int ns) {
-#pragma unroll 4
-  for (int i = t0; i < M; i += ns) {
-    const int p = list[i];
-    const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
-    const int C = (((is3d ? Z >> 1 : 0) << (lxc + lyc)) | ((Y >> 1) << lxc) | (X >> 1));
-    mark[C] = 1;
-  }
+// Extents of one level's grid (any even sizes; level l halves level l-1 along every axis,
+// z only in 3D).
+struct Ext {
+  int x, y, z;
+};
+// The cell of level l holding flat index p of level l-1.
+__device__ __forceinline__ int mg_cell(int p, Ext f, int is3d, Ext c) {
+  const int X = p % f.x, t = p / f.x, Y = t % f.y, Z = t / f.y;
+  return ((is3d ? Z >> 1 : 0) * c.y + (Y >> 1)) * c.x + (X >> 1);
 }
 
-__device__ __forceinline__ void mg_parent_body(const int* __restrict__ list, int M, int lxf, int lyf, int is3d,
-                                               int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg,
-                                               int t0, int ns) {
+// mark the cells of level l (extents c) holding nodes of level l-1 (extents f)
+__device__ __forceinline__ void mg_mark_body(const int* __restrict__ list, int M, Ext f, int is3d, Ext c,
+                                             unsigned char* __restrict__ mark, int t0, int ns) {
 #pragma unroll 4
-  for (int i = t0; i < M; i += ns) {
-    const int p = list[i];
-    const int X = p & ((1 << lxf) - 1), Y = (p >> lxf) & ((1 << lyf) - 1), Z = p >> (lxf + lyf);
-    agg[i] = cmap[((is3d ? Z >> 1 : 0) << (lxc + lyc)) | ((Y >> 1) << lxc) | (X >> 1)];
-  }
+  for (int i = t0; i < M; i += ns) mark[mg_cell(list[i], f, is3d, c)] = 1;
+}
+
+__device__ __forceinline__ void mg_parent_body(const int* __restrict__ list, int M, Ext f, int is3d, Ext c,
+                                               const int* __restrict__ cmap, int* __restrict__ agg, int t0, int ns) {
+#pragma unroll 4
+  for (int i = t0; i < M; i += ns) agg[i] = cmap[mg_cell(list[i], f, is3d, c)];
 }
 
 // Galerkin couplings of level l from level l-1.
 template <typename T>
-__device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, int M, int lxc, int lyc, int lzc,
-                                               int is3d, const unsigned char* __restrict__ fmark,
-                                               const int* __restrict__ fmap, int lxf, int lyf,
+__device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, int M, Ext ec, int is3d,
+                                               const unsigned char* __restrict__ fmark,
+                                               const int* __restrict__ fmap, Ext ef,
                                                const T* __restrict__ fc, int fcap, const int* __restrict__ cmap,
                                                T* __restrict__ c, int* __restrict__ nb, T* __restrict__ idg,
                                                int* __restrict__ child, int cap, int t0, int ns) {
-  const int mx = (1 << lxc) - 1, my = (1 << lyc) - 1, mz = (1 << lzc) - 1;
   for (int I = t0; I < M; I += ns) {
     const int C = clist[I];
-    const int X = C & mx, Y = (C >> lxc) & my, Z = C >> (lxc + lyc);
+    const int X = C % ec.x, tq = C / ec.x, Y = tq % ec.y, Z = tq / ec.y;
     T s[6] = {0, 0, 0, 0, 0, 0};
     // the 8 children's marks, then their indices, then their couplings: three rounds of
     // independent loads instead of a dependent chain per child
@@ -1273,7 +1288,7 @@ __device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, in
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int a = k & 1, b = (k >> 1) & 1, cz = k >> 2;
-      Fk[k] = (((2 * Z + cz) << (lxf + lyf)) | ((2 * Y + b) << lxf) | (2 * X + a));
+      Fk[k] = ((2 * Z + cz) * ef.y + (2 * Y + b)) * ef.x + (2 * X + a);
       mk[k] = (is3d || cz == 0) ? fmark[Fk[k]] : (unsigned char)0;
     }
 #pragma unroll
@@ -1288,9 +1303,11 @@ __device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, in
       s[b ? 2 : 3] += fc[(b ? 2 : 3) * fcap + j];
       if (is3d) s[cz ? 4 : 5] += fc[(cz ? 4 : 5) * fcap + j];
     }
-    const int ncell[6] = {(Z << (lxc + lyc)) | (Y << lxc) | ((X + 1) & mx), (Z << (lxc + lyc)) | (Y << lxc) | ((X - 1) & mx),
-                          (Z << (lxc + lyc)) | (((Y + 1) & my) << lxc) | X, (Z << (lxc + lyc)) | (((Y - 1) & my) << lxc) | X,
-                          (((Z + 1) & mz) << (lxc + lyc)) | (Y << lxc) | X, (((Z - 1) & mz) << (lxc + lyc)) | (Y << lxc) | X};
+    const int xp = X + 1 == ec.x ? 0 : X + 1, xm = X == 0 ? ec.x - 1 : X - 1;
+    const int yp = Y + 1 == ec.y ? 0 : Y + 1, ym = Y == 0 ? ec.y - 1 : Y - 1;
+    const int zp = Z + 1 == ec.z ? 0 : Z + 1, zm = Z == 0 ? ec.z - 1 : Z - 1;
+    const int ncell[6] = {(Z * ec.y + Y) * ec.x + xp, (Z * ec.y + Y) * ec.x + xm, (Z * ec.y + yp) * ec.x + X,
+                          (Z * ec.y + ym) * ec.x + X, (zp * ec.y + Y) * ec.x + X, (zm * ec.y + Y) * ec.x + X};
     T d = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
@@ -1302,31 +1319,29 @@ __device__ __forceinline__ void mg_coarse_body(const int* __restrict__ clist, in
   }
 }
 
-static __global__ void k_mg_mark(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
-                                 int is3d, int lxc, int lyc, unsigned char* __restrict__ mark) {
-  mg_mark_body(list, *cnt, lxf, lyf, is3d, lxc, lyc, mark, blockIdx.x * blockDim.x + threadIdx.x,
-               gridDim.x * blockDim.x);
+static __global__ void k_mg_mark(const int* __restrict__ list, const int* __restrict__ cnt, Ext f, int is3d, Ext c,
+                                 unsigned char* __restrict__ mark) {
+  mg_mark_body(list, *cnt, f, is3d, c, mark, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-static __global__ void k_mg_parent(const int* __restrict__ list, const int* __restrict__ cnt, int lxf, int lyf,
-                                   int is3d, int lxc, int lyc, const int* __restrict__ cmap, int* __restrict__ agg) {
-  mg_parent_body(list, *cnt, lxf, lyf, is3d, lxc, lyc, cmap, agg, blockIdx.x * blockDim.x + threadIdx.x,
-                 gridDim.x * blockDim.x);
+static __global__ void k_mg_parent(const int* __restrict__ list, const int* __restrict__ cnt, Ext f, int is3d, Ext c,
+                                   const int* __restrict__ cmap, int* __restrict__ agg) {
+  mg_parent_body(list, *cnt, f, is3d, c, cmap, agg, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 template <typename T>
-__global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict__ ccnt, int lxc, int lyc, int lzc,
-                            int is3d, const unsigned char* __restrict__ fmark, const int* __restrict__ fmap,
-                            int lxf, int lyf, const T* __restrict__ fc, int fcap, const int* __restrict__ cmap,
-                            T* __restrict__ c, int* __restrict__ nb, T* __restrict__ idg, int* __restrict__ child,
-                            int cap) {
-  mg_coarse_body<T>(clist, *ccnt, lxc, lyc, lzc, is3d, fmark, fmap, lxf, lyf, fc, fcap, cmap, c, nb, idg, child, cap,
+__global__ void k_mg_coarse(const int* __restrict__ clist, const int* __restrict__ ccnt, Ext ec, int is3d,
+                            const unsigned char* __restrict__ fmark, const int* __restrict__ fmap, Ext ef,
+                            const T* __restrict__ fc, int fcap, const int* __restrict__ cmap, T* __restrict__ c,
+                            int* __restrict__ nb, T* __restrict__ idg, int* __restrict__ child, int cap) {
+  mg_coarse_body<T>(clist, *ccnt, ec, is3d, fmark, fmap, ef, fc, fcap, cmap, c, nb, idg, child, cap,
                     blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // One level's arrays for the single-block set-up of the small levels.
 template <typename T> struct MGSetLevel {
-  int lx, ly, lz, cap;
+  Ext e;
+  int cap;
   int* cnt;
   int* list;
   int* map;
@@ -1355,7 +1370,7 @@ template <typename T> __global__ void __launch_bounds__(1024) k_mg_setup_tail(MG
     for (int i = tid; i < L.cap; i += nt) L.mark[i] = 0;
     __syncthreads();
     const int MF = *F.cnt;
-    mg_mark_body(F.list, MF, F.lx, F.ly, a.is3d, L.lx, L.ly, L.mark, tid, nt);
+    mg_mark_body(F.list, MF, F.e, a.is3d, L.e, L.mark, tid, nt);
     __syncthreads();
     const int per = (L.cap + nt - 1) / nt;
     const int lo = min(L.cap, tid * per), hi = min(L.cap, lo + per);
@@ -1380,8 +1395,8 @@ template <typename T> __global__ void __launch_bounds__(1024) k_mg_setup_tail(MG
     if (tid == nt - 1) *L.cnt = part[tid];
     __syncthreads();
     const int M = part[nt - 1];
-    mg_parent_body(F.list, MF, F.lx, F.ly, a.is3d, L.lx, L.ly, L.map, F.agg, tid, nt);
-    mg_coarse_body<T>(L.list, M, L.lx, L.ly, L.lz, a.is3d, F.mark, F.map, F.lx, F.ly, F.c, F.cap, L.map, L.c, L.nb,
+    mg_parent_body(F.list, MF, F.e, a.is3d, L.e, L.map, F.agg, tid, nt);
+    mg_coarse_body<T>(L.list, M, L.e, a.is3d, F.mark, F.map, F.e, F.c, F.cap, L.map, L.c, L.nb,
                       L.idg, L.child, L.cap, tid, nt);
     __syncthreads();
   }

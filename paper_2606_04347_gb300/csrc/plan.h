@@ -20,6 +20,12 @@ struct Error : public std::runtime_error {
                          std::string(#call) + ": " + cudaGetErrorString(e_));                \
   } while (0)
 
+// Tile options of a plan (0 = the default choice): pass-A z-planes per CTA, pass-B pencil
+// blocks per CTA, and direct pass-A loads/stores instead of tensor-copy staging.
+struct TileOpt {
+  int zb = 0, kb = 0, direct = 0;
+};
+
 class PlanBase {
  public:
   virtual ~PlanBase() {}
@@ -32,9 +38,14 @@ class PlanBase {
   virtual void remainder(int which, const void* phi, const void* phi_old, const void* u, void* out) = 0;
   virtual void timing(int enable) = 0;
   virtual void timing_read(int kind, double* ms, long* launches, double* bytes) = 0;
+  // Milliseconds per forward + inverse transform pair of the plan's grid (mean of reps, after
+  // one untimed pair), with its tiles.
+  virtual double time_transforms(int reps) = 0;
+  // The tiles in use: pass-A z-planes, pass-B pencil blocks, tensor-copy staging (1/0).
+  virtual void tiles(int* zb, int* kb, int* tma) const = 0;
 };
 
-PlanBase* make_plan_f32(const etd_params& p, cudaStream_t s);
-PlanBase* make_plan_f64(const etd_params& p, cudaStream_t s);
+PlanBase* make_plan_f32(const etd_params& p, cudaStream_t s, const TileOpt& t = TileOpt{});
+PlanBase* make_plan_f64(const etd_params& p, cudaStream_t s, const TileOpt& t = TileOpt{});
 
 }  // namespace etd

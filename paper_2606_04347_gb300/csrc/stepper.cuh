@@ -46,7 +46,10 @@ template <typename T> class Stepper : public PlanBase {
  public:
   using C = typename Cplx<T>::type;
 
-  explicit Stepper(const etd_params& P, cudaStream_t s) : P_(P), st_(s) {
+  Stepper(const etd_params& P, cudaStream_t s, const TileOpt& t = TileOpt{}) : P_(P), st_(s) {
+    tune_zb_ = t.zb;
+    tune_kb_ = t.kb;
+    tune_direct_ = t.direct;
     try {
       init();
     } catch (...) {
@@ -254,13 +257,17 @@ template <typename T> class Stepper : public PlanBase {
     while ((1 << g_.lx) < nx) ++g_.lx;
     g_.ly = 0;
     while ((1 << g_.ly) < ny) ++g_.ly;
+    auto is_pow2 = [](int v) { return (v & (v - 1)) == 0; };
+    g_.pow2 = is_pow2(nx) && is_pow2(ny) && is_pow2(nz);
     g_.n = (long long)nx * ny * nz;
     g_.nhat = (long long)g_.nxh * ny * nz;
     g_.hx = 2.0 * P_.half_len[0] / nx;
     g_.hy = 2.0 * P_.half_len[1] / ny;
     g_.hz = P_.dim == 2 ? 1.0 : 2.0 * P_.half_len[2] / nz;
     hvol_ = g_.hx * g_.hy * (P_.dim == 2 ? 1.0 : g_.hz);
-    if (!choose_tiles(g_, sizeof(C), smemA_, smemB1_))
+    if (!g_.pow2 && sizeof(T) == 4 && P_.model == ETD_MODEL_COUPLED)
+      throw Error(ETD_EINVAL, "96-point axes are not supported by the FP32-mixed coupled form");
+    if (!choose_tiles(g_, sizeof(C), smemA_, smemB1_, tune_zb_, tune_kb_))
       throw Error(ETD_EINVAL, "grid not supported by the two-pass FFT tiles");
     if ((size_t)optin < smemA_ || (size_t)optin < 2 * smemB1_) throw Error(ETD_EINVAL, "not enough shared memory");
 
@@ -510,8 +517,19 @@ template <typename T> class Stepper : public PlanBase {
   static int epi_fields(const EpiPhiGVol<T>& e) { return e.zero ? 3 : 2; }
   static int epi_fields(const EpiPhiIncVol& e) { return e.zero ? 6 : 5; }  // phi^n hi, lo read; hi, lo, G (, R2) written
 
+  // Kernel of the axis-length family (fft_family): 96-point axes have instantiations of their own.
+  template <typename Pro> auto fwd_kernel() const {
+    return fft_family(g_.nx) == 1 ? passA_fwd<T, Pro, 1> : passA_fwd<T, Pro, 0>;
+  }
+  template <typename Epi> auto inv_kernel() const {
+    return fft_family(g_.nx) == 1 ? passA_inv<T, Epi, 1> : passA_inv<T, Epi, 0>;
+  }
+  template <typename Op> auto passb_kernel() const {
+    return fft_family(g_.nz) == 1 ? passB<T, Op, 1> : passB<T, Op, 0>;
+  }
+
   template <typename Pro> void fwd(Pro pro, C* out) {
-    auto k = passA_fwd<T, Pro>;
+    auto k = fwd_kernel<Pro>();
     // tile, then (staged store) the leftover-column buffer after the barrier slot
     const size_t smem = tma_bar_off_ + 16 + (size_t)ETD_PASSA_THREADS * sizeof(C);
     set_smem((const void*)k, smem);
@@ -534,7 +552,7 @@ template <typename T> class Stepper : public PlanBase {
   }
 
   template <typename Epi> void inv(const C* in, Epi epi) {
-    auto k = passA_inv<T, Epi>;
+    auto k = inv_kernel<Epi>();
     const size_t smem = tma_bar_off_ + 16;
     set_smem((const void*)k, smem);
     PassAIn pin{0, tma_box_, (int)tma_bar_off_, status_, wait_tries_};
@@ -588,7 +606,7 @@ template <typename T> class Stepper : public PlanBase {
     tma_ok_ = false;
     // ETD_PASSA_DIRECT=1 keeps the direct loads and stores (the two forms are compared in tests)
     const char* direct = std::getenv("ETD_PASSA_DIRECT");
-    if (direct && direct[0] == '1') return;
+    if ((direct && direct[0] == '1') || tune_direct_) return;
     const int nt = ETD_PASSA_THREADS, ncols = g_.ZB * g_.nxh;
     const size_t box = (size_t)2 * g_.ZB * g_.nxh * g_.Y2 * sizeof(T);
     const bool shape = g_.nz > 1 && g_.nxh <= 256 && g_.Y2 <= 256 && (2 * g_.ZB * sizeof(T)) % 16 == 0 &&
@@ -639,7 +657,7 @@ template <typename T> class Stepper : public PlanBase {
   static int op_extra(const OpFromStd<T>&) { return 1; }
 
   template <typename Op> void passb(const Op& op, const C* in0, const C* in1, OutP<C> o) {
-    auto k = passB<T, Op>;
+    auto k = passb_kernel<Op>();
     const size_t smemB = (Op::NI >= 2 || op.nout >= 2 ? 2 : 1) * smemB1_;  // two tiles: inputs, alternating outputs
     set_smem((const void*)k, smemB);
     const int nkb = (g_.nxh + g_.KB - 1) / g_.KB;
@@ -675,6 +693,7 @@ template <typename T> class Stepper : public PlanBase {
   // Narrow band of phi: mask, ascending index list, count (device).  The previous list
   // is kept in idx_old_ so the solution can be cleared on nodes that left the band.
   void compute_band(const T* phi) {
+    cg_grid_ = 0;  // a new band: the solve's grid is the default until a frozen band sizes it
     std::swap(idx_, idx_old_);
     std::swap(count_, count_old_);
     if (g_.n % 4 == 0 && (reinterpret_cast<uintptr_t>(phi) & 15) == 0) {
@@ -800,7 +819,7 @@ template <typename T> class Stepper : public PlanBase {
     int per = 0;
     ETD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 1024, 0));
     if (per < 1) throw Error(ETD_ECUDA, "band CG kernel cannot be resident");
-    const int grid = nsm_;
+    const int grid = cg_grid_ > 0 ? cg_grid_ : nsm_;
     const int* idx = idx_;
     const int* cnt = count_;
     T* wfull = x;
@@ -815,12 +834,8 @@ template <typename T> class Stepper : public PlanBase {
   // Jacobi weights, the coarse-grid correction over-corrected by 1.9 (piecewise-constant
   // aggregation under-estimates it) and 2 sweeps on the coarsest level.
   void init_multigrid() {
-    int lz = 0;
-    while ((1 << lz) < g_.nz) ++lz;
     HostLevel& L0 = lv_[0];
-    L0.lx = g_.lx;
-    L0.ly = g_.ly;
-    L0.lz = lz;
+    L0.ext = Ext{g_.nx, g_.ny, g_.nz};
     L0.cap = (int)g_.n;
     L0.agg = alloc<int>(g_.n);
     L0.e = alloc<T>(g_.n);
@@ -831,12 +846,12 @@ template <typename T> class Stepper : public PlanBase {
     const bool is3d = g_.nz > 1;
     while (mg_nlev_ < kMGMax) {
       const HostLevel& F = lv_[mg_nlev_ - 1];
-      if (F.lx < 3 || F.ly < 3 || (is3d && F.lz < 3)) break;
+      // coarsen while every extent is even and at least 8
+      auto ok = [](int v) { return v >= 8 && v % 2 == 0; };
+      if (!ok(F.ext.x) || !ok(F.ext.y) || (is3d && !ok(F.ext.z))) break;
       HostLevel& L = lv_[mg_nlev_];
-      L.lx = F.lx - 1;
-      L.ly = F.ly - 1;
-      L.lz = is3d ? F.lz - 1 : 0;
-      L.cap = 1 << (L.lx + L.ly + L.lz);
+      L.ext = Ext{F.ext.x / 2, F.ext.y / 2, is3d ? F.ext.z / 2 : 1};
+      L.cap = L.ext.x * L.ext.y * L.ext.z;
       L.nblk = (L.cap + kCompactBlock - 1) / kCompactBlock;
       L.cnt = alloc<int>(1);
       L.list = alloc<int>(L.cap);
@@ -876,8 +891,8 @@ template <typename T> class Stepper : public PlanBase {
       int* fagg = lv_[l - 1].agg;
       timed(ETD_K_BAND, 0.0, [&] {
         ETD_CUDA(cudaMemsetAsync(L.mark, 0, L.cap, st_));
-        k_mg_mark<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.lx, F.ly, is3d, L.lx, L.ly, L.mark);
-        if (L.cap % 4 == 0) {  // level grids are powers of two of at least 2^15 cells here
+        k_mg_mark<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.ext, is3d, L.ext, L.mark);
+        if (L.cap % 4 == 0) {  // levels here have at least 2^15 cells, x extent even
           const int nb4 = (int)(((long long)L.cap + kCompactWide - 1) / kCompactWide);
           k_mask_count4<<<nb4, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount);
           k_band_scan<<<1, 1024, 0, st_>>>(nb4, L.bcount, L.cnt);
@@ -887,8 +902,8 @@ template <typename T> class Stepper : public PlanBase {
           k_band_scan<<<1, 1024, 0, st_>>>(L.nblk, L.bcount, L.cnt);
           k_band_scatter<<<L.nblk, kCompactBlock, 0, st_>>>(L.cap, L.mark, L.bcount, L.list, L.map);
         }
-        k_mg_parent<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.lx, F.ly, is3d, L.lx, L.ly, L.map, fagg);
-        k_mg_coarse<T><<<nsm_ * 4, 256, 0, st_>>>(L.list, L.cnt, L.lx, L.ly, L.lz, is3d, fmark, fmap, F.lx, F.ly, fc,
+        k_mg_parent<<<nsm_ * 4, 256, 0, st_>>>(flist, fcnt, F.ext, is3d, L.ext, L.map, fagg);
+        k_mg_coarse<T><<<nsm_ * 4, 256, 0, st_>>>(L.list, L.cnt, L.ext, is3d, fmark, fmap, F.ext, fc,
                                                   F.cap, L.map, L.c, L.nb, L.idg, L.child, L.cap);
       });
       ETD_CUDA(cudaGetLastError());
@@ -901,9 +916,7 @@ template <typename T> class Stepper : public PlanBase {
       for (int k = 0; k < mg_nlev_; ++k) {
         const HostLevel& H = lv_[k];
         MGSetLevel<T>& S = a.L[k];
-        S.lx = H.lx;
-        S.ly = H.ly;
-        S.lz = H.lz;
+        S.e = H.ext;
         S.cap = H.cap;
         S.agg = H.agg;
         if (k == 0) {
@@ -1144,6 +1157,12 @@ template <typename T> class Stepper : public PlanBase {
       launch_grid(k_gloc<T>, g_.n, (const T*)phiA_, G_);
       band_for_solve(phiA_, G_);
       fixed_ready_ = true;
+      // the frozen band's size sets the band solve's grid: about 2048 nodes per block of 1024
+      // threads, so that small bands leave SMs to concurrent work (one read, once per membrane)
+      int cnt = 0;
+      ETD_CUDA(cudaMemcpyAsync(&cnt, count_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+      ETD_CUDA(cudaStreamSynchronize(st_));
+      cg_grid_ = std::max(1, std::min(nsm_, (cnt + 2047) / 2048));
       band_dirty_ = false;
     }
     for (int n = 0; n < nsteps; ++n) {
@@ -1172,6 +1191,36 @@ template <typename T> class Stepper : public PlanBase {
 
   // ------------------------------------------------------------------ timing
  public:
+  double time_transforms(int reps) override {
+    // forward: field -> spectrum (plan layout); inverse: spectrum -> field (identity multiplier)
+    auto pair = [&] {
+      forward_store(phiA_, sS_);
+      OpDeriv<T> op{1, {0, 0, 0, 0, 0}, sS_, sk_};
+      passb(op, nullptr, nullptr, outs({I_[0]}));
+      inv(I_[0], EpiStore<T>{phiB_});
+    };
+    pair();
+    cudaEvent_t a, b;
+    ETD_CUDA(cudaEventCreate(&a));
+    ETD_CUDA(cudaEventCreate(&b));
+    ETD_CUDA(cudaEventRecord(a, st_));
+    for (int r = 0; r < reps; ++r) pair();
+    ETD_CUDA(cudaEventRecord(b, st_));
+    ETD_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    ETD_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    sync_check();
+    return ms / std::max(reps, 1);
+  }
+
+  void tiles(int* zb, int* kb, int* tma) const override {
+    *zb = g_.ZB;
+    *kb = g_.KB;
+    *tma = tma_ok_ ? 1 : 0;
+  }
+
   void timing(int enable) override {
     if (enable) {
       if (ev_.empty()) {
@@ -1259,6 +1308,9 @@ template <typename T> class Stepper : public PlanBase {
   T c_lap_{};
   double hvol_ = 1.0;
   int nsm_ = 1;
+  int tune_zb_ = 0, tune_kb_ = 0;           // requested pass-A z-planes / pass-B pencil blocks (0: default)
+  int tune_direct_ = 0;                      // 1: direct pass-A loads/stores (no tensor-copy staging)
+  int cg_grid_ = 0;                          // blocks of the band solve (0: one per SM)
   long long wait_budget_ = 4000000000LL;   // grid barrier: clock cycles before ETD_ETIMEOUT
   long long wait_tries_ = 1LL << 22;       // pass-A tensor copy: mbarrier polls before ETD_ETIMEOUT
   size_t smemA_ = 0, smemB1_ = 0;
@@ -1281,7 +1333,8 @@ template <typename T> class Stepper : public PlanBase {
   double *csize_ = nullptr, *csum_ = nullptr;
   // multigrid hierarchy of the band solve (level 0 = the band itself)
   struct HostLevel {
-    int lx = 0, ly = 0, lz = 0, cap = 0, nblk = 0;
+    Ext ext{1, 1, 1};   // grid extents of the level
+    int cap = 0, nblk = 0;
     int *cnt = nullptr, *list = nullptr, *map = nullptr, *bcount = nullptr;
     unsigned char* mark = nullptr;
     T *c = nullptr, *idg = nullptr, *b = nullptr, *e = nullptr, *o = nullptr, *t = nullptr;

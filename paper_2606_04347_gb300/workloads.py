@@ -130,7 +130,7 @@ def band_of(phi, hi=0.99):
 #   c1  2D fixed membrane, ETD1, FP64, 128^2, circle R = 0.6 pi, eps = 0.05, seed 0
 #   c2  3D fixed membrane, ETDRK2, 128^3, sphere R = 0.5 pi, eps = 0.05, seed 1
 #   c3  3D coupled, ETDRK2, 256^3, ellipsoid (1.2, 0.9, 0.9), eps = 0.18, seed 2
-#   c4  batched fixed-membrane sweep (64^3/96^3/128^3), seeds 100-147
+#   c4  batched fixed-membrane sweep (64^3/96^3/128^3), seeds 100-147 (c4_run)
 #   c5  3D coupled, 512^3, two spheres R = 0.8, 0.6 at (+-0.8, 0, 0), seed 3
 # Every configuration lives on [-pi, pi)^d.  `n` overrides the grid (same physical setup
 # on a coarser grid, e.g. c3 at 64^3 for the oracle).
@@ -190,6 +190,28 @@ def workload(name: str, n: Optional[int] = None, precision: int = 0, scheme=None
         u = np.where(band_of(phi), 0.5 * (1.0 + xi), 0.5)
         return p, phi, u, 2000
     raise KeyError(name)
+
+
+def c4_run(seed: int, precision: int = 1):
+    """One run of the batched fixed-membrane sweep: (params, Phi0, U0, nsteps).
+
+    Seeds 100-147 make the 48 runs.  From the seed: the grid N^3 with N in {64, 96, 128}, the
+    interface width eps in [0.03, 0.08], the nonlocal strength sigma = gamma in [10, 200], the
+    stabiliser factor S in {1, 2, 4}, and tau in {1e-3, 2e-3, 5e-3}; B2 = 4000 S; sphere
+    membrane R = 0.5 pi, U0 = (1 + clip(0.1 N(0,1)))/2, ETDRK2, 200 steps, M = 200,
+    ubar = 0.5, B1 = 1 (the fixed-model coefficients of c2).
+    """
+    rng = np.random.default_rng(seed)
+    N = int(rng.choice([64, 96, 128]))
+    eps = float(rng.uniform(0.03, 0.08))
+    gamma = float(rng.uniform(10.0, 200.0))
+    S = int(rng.choice([1, 2, 4]))
+    tau = float(rng.choice([1e-3, 2e-3, 5e-3]))
+    p = _fixed_params(3, (N, N, N), eps, 2, 200.0, tau, precision)
+    p = p.replace(gamma=gamma, B2=4000.0 * S)
+    phi = sphere_phi(p, 0.5 * math.pi, eps)
+    u = 0.5 * (1.0 + np.clip(0.1 * rng.standard_normal(size=p.shape), -1.0, 1.0))
+    return p, phi, u, 200
 
 
 def random_fields(shape, seed, lo=0.0, hi=1.0):

@@ -69,7 +69,7 @@ def _plan_status(lib, p):
 
 
 @pytest.mark.parametrize("change", [
-    dict(dim=4), dict(n=(48, 64, 64)), dict(n=(512, 64, 64)), dict(n=(64, 64, 4)),
+    dict(dim=4), dict(n=(48, 64, 64)), dict(n=(512, 64, 64)), dict(n=(64, 64, 4)), dict(n=(64, 192, 64)),
     dict(half_len=(math.pi, 2.0, math.pi)), dict(tau=0.0), dict(eps_u=-1.0), dict(scheme=3),
     dict(precision=7), dict(cg_maxit=0), dict(band_mask_hi=1.5),
 ])
