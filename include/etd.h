@@ -6,6 +6,12 @@
  * The library advances the phase field phi (membrane) and the protein density u on a
  * periodic 2D/3D grid with the FFT-based stabilised ETD1/ETDRK2 schemes of Sec. 3.3 and
  * Algorithm 1, or (model = ETD_MODEL_FIXED) the protein density alone on a frozen membrane.
+ * model = ETD_MODEL_FIXED_SQRTG runs the frozen-membrane scheme of Sec. 2.2 instead: the
+ * equation divided by g^{1/2}, d(g^{1/2} u)/dt + L_phi (g^{1/2} u) = R_phi(u) with
+ * L_phi = B - eps_u g^{-1/2} Delta_{S,h} g^{-1/2} (B = params.B2), ETD1 (Eq. (2.8)) or ETDRK2
+ * (Eq. (2.9)-(2.10)), on the narrow band with zero-flux band edges; phi_j(tau L_phi) acts
+ * through Lanczos Krylov spaces (L_phi is not diagonal in Fourier space).  u off the band is
+ * left unchanged.
  *
  * Conventions shared by every entry point:
  *  - Fields are dense, C-ordered, x fastest: index (k*Ny + j)*Nx + i for 3D, j*Nx + i for
@@ -47,7 +53,11 @@ typedef enum {
 } etd_status;
 
 typedef enum { ETD_ETD1 = 1, ETD_ETDRK2 = 2 } etd_scheme;
-typedef enum { ETD_MODEL_FIXED = 0, ETD_MODEL_COUPLED = 1 } etd_model;
+typedef enum {
+  ETD_MODEL_FIXED = 0,        /* frozen membrane, FFT-diagonal split of Sec. 3 (Eq. (2.1))    */
+  ETD_MODEL_COUPLED = 1,      /* phi-u system, Algorithm 1                                   */
+  ETD_MODEL_FIXED_SQRTG = 2   /* frozen membrane, g^{1/2}-split scheme of Sec. 2.2 (Krylov)   */
+} etd_model;
 typedef enum { ETD_FP64 = 0, ETD_FP32_MIXED = 1 } etd_precision;
 
 /* Problem statement (Sec. 1 model, Sec. 3.1 splittings, Sec. 3.3 schemes). */
@@ -71,6 +81,11 @@ typedef struct {
   double cg_rtol_pred;     /* ETDRK2 only: relative residual of the predictor-stage
                               band solves, whose result reaches u^{n+1} only through the
                               corrector's tau phi2 (R2(U~) - R2(U^n)) term; 0 = cg_rtol  */
+  double krylov_tol;       /* ETD_MODEL_FIXED_SQRTG: a Krylov space grows (8 Lanczos steps
+                              at a time, at most 128) until the estimated error of
+                              tau phi_j(tau L_phi) x, |x| beta_m tau |e_m^T phi_{j+1}(tau T_m) e_1|,
+                              is below krylov_tol times the result's norm; 0 = 1e-12 (FP64),
+                              1e-6 (FP32-mixed).  Ignored by the other models.              */
 } etd_params;
 
 /* Diagnostics of the current state (Eq. (2.16) energy and the bound of Sec. 2.2). */
@@ -84,6 +99,7 @@ typedef struct {
   long band_size;          /* number of band nodes                                     */
   int cg_iters_last;       /* iterations of the last band solve                        */
   double cg_resid_last;    /* relative residual reached by the last band solve         */
+  int krylov_dim_last;     /* ETD_MODEL_FIXED_SQRTG: largest Krylov dimension of the call  */
 } etd_diag;
 
 /* Create a plan: validates `params`, allocates the workspace on the current device and
@@ -157,7 +173,7 @@ etd_status etd_nonlocal(etd_plan_t plan, const void *phi, const void *f, void *w
 etd_status etd_remainder(etd_plan_t plan, int which, const void *phi, const void *phi_old,
                          const void *u, void *out);
 
-/* ---- Batched runs (many independent simulations, Sec. 2 fixed model or Sec. 3 coupled) -- */
+/* ---- Batched runs (many independent simulations, fixed model or coupled) -------------- */
 
 typedef struct etd_batch_s *etd_batch_t;
 
@@ -168,7 +184,9 @@ typedef struct etd_batch_s *etd_batch_t;
  * transform pair for each candidate tiling (pass-A z-planes per block, pass-B pencil blocks
  * per block, tensor-copy staging of pass A on or off) and give the runs of that grid the
  * fastest; 0: default tiles.  Tiling never changes the results (the same arithmetic per
- * element).  Synchronous; ETD_EINVAL names the first invalid run. */
+ * element).  Runs of model ETD_MODEL_FIXED_SQRTG are rejected (ETD_EINVAL): their Krylov
+ * spaces are sized on the host between launches, which a recorded graph cannot do.
+ * Synchronous; ETD_EINVAL names the first invalid run. */
 etd_status etd_plan_batch(const etd_params *params, int nruns, void *cuda_stream, int autotune_tiles,
                           etd_batch_t *out);
 
@@ -205,7 +223,8 @@ typedef enum {
   ETD_K_POINTWISE = 4,   /* R1, R2, Delta_S u and other full-grid pointwise kernels      */
   ETD_K_BAND = 5,        /* band compaction and CG set-up                                */
   ETD_K_REDUCE = 6,      /* FP64 reductions                                              */
-  ETD_K_NKINDS = 7
+  ETD_K_KRYLOV = 7,      /* Lanczos steps, Krylov norms and combinations (Sec. 2.2 scheme) */
+  ETD_K_NKINDS = 8
 } etd_kernel_kind;
 
 /* enable = 1: reset the counters and bracket every later launch with CUDA events on the

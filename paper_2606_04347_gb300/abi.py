@@ -35,7 +35,7 @@ class etd_params(ct.Structure):
         ("A1", ct.c_double), ("A2", ct.c_double), ("B1", ct.c_double), ("B2", ct.c_double),
         ("band_mask_hi", ct.c_double), ("recover_delta", ct.c_double),
         ("cg_rtol", ct.c_double), ("cg_maxit", ct.c_int), ("linear_only", ct.c_int),
-        ("cg_rtol_pred", ct.c_double),
+        ("cg_rtol_pred", ct.c_double), ("krylov_tol", ct.c_double),
     ]
 
 
@@ -44,6 +44,7 @@ class etd_diag(ct.Structure):
         ("energy", ct.c_double), ("mass", ct.c_double), ("max_bound", ct.c_double),
         ("umin", ct.c_double), ("umax", ct.c_double), ("volume", ct.c_double),
         ("band_size", ct.c_long), ("cg_iters_last", ct.c_int), ("cg_resid_last", ct.c_double),
+        ("krylov_dim_last", ct.c_int),
     ]
 
     def as_dict(self):
@@ -83,7 +84,7 @@ SIGNATURES.update({
 SIGNATURES["etd_fft_forward_noalloc"] = (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.c_int, ct.c_void_p,
                                                   ct.c_void_p, ct.c_void_p])
 
-KERNEL_KINDS = ["fft_a_fwd", "fft_a_inv", "fft_b", "cg", "pointwise", "band", "reduce"]
+KERNEL_KINDS = ["fft_a_fwd", "fft_a_inv", "fft_b", "cg", "pointwise", "band", "reduce", "krylov"]
 
 
 def load_library(path: str = LIB_PATH):

@@ -65,7 +65,10 @@ etd_status validate(const etd_params& p) {
     if (std::fabs(p.half_len[d] - p.half_len[0]) > 1e-12 * p.half_len[0])
       return fail(ETD_EINVAL, "only cubic boxes (X = Y = Z) are supported");
   if (p.scheme != ETD_ETD1 && p.scheme != ETD_ETDRK2) return fail(ETD_EINVAL, "scheme must be ETD1 or ETDRK2");
-  if (p.model != ETD_MODEL_FIXED && p.model != ETD_MODEL_COUPLED) return fail(ETD_EINVAL, "unknown model");
+  if (p.model != ETD_MODEL_FIXED && p.model != ETD_MODEL_COUPLED && p.model != ETD_MODEL_FIXED_SQRTG)
+    return fail(ETD_EINVAL, "unknown model");
+  if (p.model == ETD_MODEL_FIXED_SQRTG && !(p.B2 > 0)) return fail(ETD_EINVAL, "the Sec. 2.2 scheme needs B = B2 > 0");
+  if (!(p.krylov_tol >= 0) || !(p.krylov_tol < 1)) return fail(ETD_EINVAL, "krylov_tol must be in [0, 1)");
   if (p.model == ETD_MODEL_COUPLED && p.dim != 3) return fail(ETD_EINVAL, "the coupled model is 3D");
   if (p.precision != ETD_FP64 && p.precision != ETD_FP32_MIXED) return fail(ETD_EINVAL, "unknown precision");
   if (!(p.tau > 0) || !(p.eps_u > 0) || !(p.eps_phi > 0)) return fail(ETD_EINVAL, "tau and eps must be positive");
@@ -317,6 +320,10 @@ etd_status etd_plan_batch(const etd_params* params, int nruns, void* cuda_stream
   for (int i = 0; i < nruns; ++i) {
     const etd_status v = validate(params[i]);
     if (v != ETD_OK) return fail(v, "run " + std::to_string(i) + ": " + g_last_error);
+    if (params[i].model == ETD_MODEL_FIXED_SQRTG)
+      return fail(ETD_EINVAL, "run " + std::to_string(i) +
+                                  ": the Sec. 2.2 scheme sizes its Krylov spaces on the host between launches and "
+                                  "cannot run inside a batch graph; use etd_plan");
   }
   etd_batch_s* b = new etd_batch_s;
   b->user = static_cast<cudaStream_t>(cuda_stream);

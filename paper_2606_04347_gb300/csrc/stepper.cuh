@@ -7,6 +7,7 @@
 #include <cstring>
 #include <vector>
 #include "kernels.cuh"
+#include "krylov.cuh"
 #include "ops.cuh"
 #include "plan.h"
 
@@ -69,6 +70,8 @@ template <typename T> class Stepper : public PlanBase {
     if (P_.model == ETD_MODEL_COUPLED) {
       if (!phi) throw Error(ETD_EINVAL, "coupled model needs phi");
       run_coupled(static_cast<T*>(phi), static_cast<T*>(u), nsteps);
+    } else if (P_.model == ETD_MODEL_FIXED_SQRTG) {
+      run_sqrtg(static_cast<const T*>(phi), static_cast<T*>(u), nsteps);
     } else {
       run_fixed(static_cast<const T*>(phi), static_cast<T*>(u), nsteps);
     }
@@ -94,6 +97,7 @@ template <typename T> class Stepper : public PlanBase {
       last->cg_resid_last = rs;
       last->volume = hvol_ * sc[S_VOL];
       last->mass = hvol_ * sc[S_MASS];
+      last->krylov_dim_last = kry_dim_max_;
       if (h[1]) throw Error(ETD_ENONFINITE, "non-finite value in the state");
       check_status(h[0]);
     }
@@ -451,6 +455,9 @@ template <typename T> class Stepper : public PlanBase {
   void release() {
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
+    if (kry_mem_) cudaFree(kry_mem_);
+    kry_mem_ = nullptr;
+    kry_cap_ = 0;
     if (fork_ev_) cudaEventDestroy(fork_ev_);
     if (join_ev_) cudaEventDestroy(join_ev_);
     if (side_) cudaStreamDestroy(side_);
@@ -683,7 +690,7 @@ template <typename T> class Stepper : public PlanBase {
     if (s == 0) return;
     ETD_CUDA(cudaMemset(status_, 0, sizeof(int)));
     if (s == 5) throw Error(ETD_ENOTCONV, "band CG did not reach cg_rtol within cg_maxit iterations");
-    if (s == 6) throw Error(ETD_ETIMEOUT, "grid barrier of the band CG timed out");
+    if (s == 6) throw Error(ETD_ETIMEOUT, "a grid barrier of the band CG or the Lanczos process timed out");
     if (s == 7) throw Error(ETD_ETIMEOUT, "a tensor copy of the FFT pass A did not complete");
     if (s == 8) throw Error(ETD_EINVAL, "the band has more connected components than the band solve supports (4096)");
     throw Error(ETD_ECUDA, "device status word set");
@@ -1146,25 +1153,32 @@ template <typename T> class Stepper : public PlanBase {
   }
 
   // ------------------------------------------------------------------ the fixed step
-  void run_fixed(const T* phi, T* u, int nsteps) {
-    const bool rk2 = P_.scheme == ETD_ETDRK2;
+  // Fixed membrane: G = g(phi) and the band come from the phi of the first call (or of a
+  // later call that passes one).  Returns true when they were (re)built.
+  bool freeze_membrane(const T* phi) {
     if (phi) {
       ETD_CUDA(cudaMemcpyAsync(phiA_, phi, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
       fixed_ready_ = false;
     }
-    if (!fixed_ready_ || band_dirty_) {
-      if (!phi && !fixed_ready_) throw Error(ETD_EINVAL, "fixed model: the first call must pass phi");
-      launch_grid(k_gloc<T>, g_.n, (const T*)phiA_, G_);
-      band_for_solve(phiA_, G_);
-      fixed_ready_ = true;
-      // the frozen band's size sets the band solve's grid: about 2048 nodes per block of 1024
-      // threads, so that small bands leave SMs to concurrent work (one read, once per membrane)
-      int cnt = 0;
-      ETD_CUDA(cudaMemcpyAsync(&cnt, count_, sizeof(int), cudaMemcpyDeviceToHost, st_));
-      ETD_CUDA(cudaStreamSynchronize(st_));
-      cg_grid_ = std::max(1, std::min(nsm_, (cnt + 2047) / 2048));
-      band_dirty_ = false;
-    }
+    if (fixed_ready_ && !band_dirty_) return false;
+    if (!phi && !fixed_ready_) throw Error(ETD_EINVAL, "fixed model: the first call must pass phi");
+    launch_grid(k_gloc<T>, g_.n, (const T*)phiA_, G_);
+    band_for_solve(phiA_, G_);
+    fixed_ready_ = true;
+    // the frozen band's size sets the band solve's grid: about 2048 nodes per block of 1024
+    // threads, so that small bands leave SMs to concurrent work (one read, once per membrane)
+    int cnt = 0;
+    ETD_CUDA(cudaMemcpyAsync(&cnt, count_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    ETD_CUDA(cudaStreamSynchronize(st_));
+    fixed_count_ = cnt;
+    cg_grid_ = std::max(1, std::min(nsm_, (cnt + 2047) / 2048));
+    band_dirty_ = false;
+    return true;
+  }
+
+  void run_fixed(const T* phi, T* u, int nsteps) {
+    const bool rk2 = P_.scheme == ETD_ETDRK2;
+    freeze_membrane(phi);
     for (int n = 0; n < nsteps; ++n) {
       ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
       launch_reduce(2, u, G_, scal_ + S_MASS);
@@ -1185,6 +1199,173 @@ template <typename T> class Stepper : public PlanBase {
         passb(ucorr, I_[0], nullptr, outs({I_[0]}));
       }
       inv(I_[0], EpiRecover<T>{u, G_, u, mc_.delta});
+    }
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  // ---- the g^{1/2}-split scheme of Sec. 2.2 (model ETD_MODEL_FIXED_SQRTG) -------------
+  // Krylov workspace for the frozen band of fixed_count_ nodes: the Lanczos basis
+  // (kKrylovMax + 1 vectors), w, R0, b, V~, g^{1/2}, g^{-1/2} (compact) and FP64 scalars.
+  void krylov_setup() {
+    const long long M = std::max(fixed_count_, 1);
+    if (M > kry_cap_) {
+      if (kry_mem_) ETD_CUDA(cudaFree(kry_mem_));
+      kry_mem_ = nullptr;
+      kry_cap_ = 0;
+      const size_t ld = (size_t)((M + 31) / 32 * 32);
+      const size_t vec = sizeof(T) * ld;
+      const size_t bytes = vec * (kKrylovMax + 1 + 6) + sizeof(double) * (5 * kKrylovMax + 1);
+      if (cudaMalloc(&kry_mem_, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        kry_mem_ = nullptr;
+        throw Error(ETD_ENOMEM, "Krylov workspace does not fit");
+      }
+      char* q = static_cast<char*>(kry_mem_);
+      kV_ = reinterpret_cast<T*>(q);
+      q += vec * (kKrylovMax + 1);
+      T** v[] = {&kw_, &kR0_, &kb_, &kVt_, &ksg_, &kisg_};
+      for (T** x : v) {
+        *x = reinterpret_cast<T*>(q);
+        q += vec;
+      }
+      double* d = reinterpret_cast<double*>(q);
+      kal_ = d;
+      kbe_ = d + kKrylovMax;
+      kacc_ = d + 2 * kKrylovMax;
+      ky_ = d + 4 * kKrylovMax;
+      knrm_ = d + 5 * kKrylovMax;
+      kld_ = (int)ld;
+      kry_cap_ = M;
+    }
+    timed(ETD_K_BAND, 3.0 * sizeof(T) * fixed_count_, [&] {
+      k_sec2_sqrtg<T><<<grid_for(fixed_count_), 256, 0, st_>>>(idx_, count_, G_, ksg_, kisg_);
+    });
+    ETD_CUDA(cudaGetLastError());
+  }
+
+  KrylovOp<T> kop() const { return KrylovOp<T>{cg_, kisg_, (T)P_.B2, (T)P_.eps_u}; }
+
+  // Lanczos steps j0 .. j1-1 in one cooperative launch.
+  void lanczos(int j0, int j1) {
+    KrylovOp<T> op = kop();
+    CGCtl c{};
+    c.acc = kacc_;
+    c.bar = bar_;
+    c.status = status_;
+    c.budget = wait_budget_;
+    ETD_CUDA(cudaMemsetAsync(bar_, 0, sizeof(unsigned) * 2, st_));
+    auto k = k_lanczos<T>;
+    int per = 0;
+    ETD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 1024, 0));
+    if (per < 1) throw Error(ETD_ECUDA, "Lanczos kernel cannot be resident");
+    const int grid = cg_grid_ > 0 ? cg_grid_ : nsm_;
+    const int* cnt = count_;
+    T* V = kV_;
+    int ld = kld_;
+    T* w = kw_;
+    double *al = kal_, *be = kbe_, *acc = kacc_;
+    void* args[] = {&cnt, &op, &V, &ld, &w, &al, &be, &acc, &j0, &j1, &c};
+    const double bytes = (double)fixed_count_ * (j1 - j0) * (15.0 * sizeof(T) + 24.0);
+    timed(ETD_K_KRYLOV, bytes, [&] {
+      ETD_CUDA(cudaLaunchCooperativeKernel((const void*)k, grid, 1024, args, 0, st_));
+    });
+  }
+
+  // tau phi_j(tau L) x for the compact vector x: the Lanczos process from x / |x| grown in
+  // chunks of kKrylovChunk steps until the estimated error of the omitted term,
+  // |x| beta_m tau |e_m^T phi_{j+1}(tau T_m) e_1|, is below krylov_tol relative to the result
+  // (or the process breaks down: an invariant subspace).  Leaves the combination weights
+  // tau |x| phi_j(tau T_m) e_1 in ky_ and returns m (0 when x = 0).
+  int krylov_phi(int j, const T* x) {
+    const int nb = grid_for(fixed_count_);
+    ETD_CUDA(cudaMemsetAsync(knrm_, 0, sizeof(double), st_));
+    timed(ETD_K_KRYLOV, (double)sizeof(T) * fixed_count_,
+          [&] { k_band_norm2<T><<<nb, 256, 0, st_>>>(count_, x, knrm_); });
+    double n2 = 0.0;
+    ETD_CUDA(cudaMemcpyAsync(&n2, knrm_, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    ETD_CUDA(cudaStreamSynchronize(st_));
+    if (!std::isfinite(n2)) throw Error(ETD_ENONFINITE, "non-finite value in a Krylov start vector");
+    if (n2 == 0.0) return 0;
+    const double beta0 = std::sqrt(n2);
+    timed(ETD_K_KRYLOV, 2.0 * sizeof(T) * fixed_count_,
+          [&] { k_band_normalise<T><<<nb, 256, 0, st_>>>(count_, x, knrm_, kV_); });
+    ETD_CUDA(cudaMemsetAsync(kacc_, 0, sizeof(double) * 2 * kKrylovMax, st_));
+    const double tol = P_.krylov_tol > 0 ? P_.krylov_tol : (sizeof(T) == 8 ? 1e-12 : 1e-6);
+    double ha[kKrylovMax], hb[kKrylovMax];
+    std::vector<double> y;
+    int m = 0, dim = 0;
+    for (;;) {
+      const int j1 = std::min(m + kKrylovChunk, kKrylovMax);
+      lanczos(m, j1);
+      ETD_CUDA(cudaMemcpyAsync(ha + m, kal_ + m, sizeof(double) * (j1 - m), cudaMemcpyDeviceToHost, st_));
+      ETD_CUDA(cudaMemcpyAsync(hb + m, kbe_ + m, sizeof(double) * (j1 - m), cudaMemcpyDeviceToHost, st_));
+      sync_check();
+      dim = j1;
+      bool invariant = false;
+      for (int k = m; k < j1; ++k) {
+        if (!std::isfinite(ha[k]) || !std::isfinite(hb[k]))
+          throw Error(ETD_ENONFINITE, "non-finite Lanczos coefficient");
+        if (!(hb[k] > 0.0)) {
+          dim = k + 1;
+          invariant = true;
+          break;
+        }
+      }
+      const double tail = krylov_coeffs(dim, ha, hb, P_.tau, j, y);
+      double ny = 0.0;
+      for (double v : y) ny += v * v;
+      const double err = hb[dim - 1] * P_.tau * tail;
+      if (invariant || err <= tol * std::sqrt(ny)) break;
+      if (j1 == kKrylovMax)
+        throw Error(ETD_ENOTCONV, "the Krylov space of phi_j(tau L) did not converge within 128 Lanczos steps");
+      m = j1;
+    }
+    for (double& v : y) v *= P_.tau * beta0;
+    ETD_CUDA(cudaMemcpyAsync(ky_, y.data(), sizeof(double) * dim, cudaMemcpyHostToDevice, st_));
+    ETD_CUDA(cudaStreamSynchronize(st_));   // y is a host temporary
+    kry_dim_max_ = std::max(kry_dim_max_, dim);
+    return dim;
+  }
+
+  // One call of Sec. 2.2's scheme on the frozen band: per step the band solve of
+  // (-Delta_S) w = g f(U) (and mass), R0 = R_phi(U), b = R0 - L V, V~ = V + tau phi_1(tau L) b;
+  // ETDRK2 then the solve at U~, d = R_phi(U~) - R0 and V = V~ + tau phi_2(tau L) d.
+  void run_sqrtg(const T* phi, T* u, int nsteps) {
+    const bool rk2 = P_.scheme == ETD_ETDRK2;
+    if (freeze_membrane(phi) || !kry_mem_) krylov_setup();
+    if (rk2) ETD_CUDA(cudaMemcpyAsync(ut_, u, sizeof(T) * g_.n, cudaMemcpyDeviceToDevice, st_));
+    const KrylovOp<T> op = kop();
+    const int nb = grid_for(fixed_count_);
+    const double M = (double)fixed_count_;
+    kry_dim_max_ = 0;
+    const bool nl = !P_.linear_only;   // the band solve and mass feed only the remainder
+    for (int n = 0; n < nsteps; ++n) {
+      if (nl) {
+        ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+        launch_reduce(2, u, G_, scal_ + S_MASS);
+        cg_solve(RhsGF<T>{G_, u}, w_, next_guess(false, rk2), rk2 ? P_.cg_rtol_pred : 0.0);
+      }
+      timed(ETD_K_POINTWISE, M * (11.0 * sizeof(T) + 32.0), [&] {
+        k_sec2_first<T><<<nb, 256, 0, st_>>>(idx_, count_, mc_, op, ksg_, u, w_, scal_, hvol_, kR0_, kb_);
+      });
+      const int m1 = krylov_phi(1, kb_);
+      timed(ETD_K_KRYLOV, M * ((m1 + 2.0 + (rk2 ? 1 : 0)) * sizeof(T) + 4.0), [&] {
+        k_krylov_finish<T><<<nb, 256, 0, st_>>>(idx_, count_, kV_, kld_, ky_, m1, nullptr, ksg_, u,
+                                                rk2 ? kVt_ : nullptr, rk2 ? ut_ : u);
+      });
+      if (!rk2) continue;
+      if (nl) {
+        ETD_CUDA(cudaMemsetAsync(scal_ + S_MASS, 0, sizeof(double), st_));
+        launch_reduce(2, ut_, G_, scal_ + S_MASS);
+        cg_solve(RhsGF<T>{G_, ut_}, w_, next_guess(true, rk2));
+      }
+      timed(ETD_K_POINTWISE, M * (5.0 * sizeof(T) + 4.0), [&] {
+        k_sec2_second<T><<<nb, 256, 0, st_>>>(idx_, count_, mc_, ksg_, ut_, w_, scal_, hvol_, kR0_, kb_);
+      });
+      const int m2 = krylov_phi(2, kb_);
+      timed(ETD_K_KRYLOV, M * ((m2 + 3.0) * sizeof(T) + 4.0), [&] {
+        k_krylov_finish<T><<<nb, 256, 0, st_>>>(idx_, count_, kV_, kld_, ky_, m2, kVt_, ksg_, nullptr, nullptr, u);
+      });
     }
     ETD_CUDA(cudaGetLastError());
   }
@@ -1360,6 +1541,13 @@ template <typename T> class Stepper : public PlanBase {
   dcomplex *twx_d_ = nullptr, *twy_d_ = nullptr, *twz_d_ = nullptr;
   T* philo_ = nullptr;
   int hP_ = -1, hC_ = -1, hO_ = -1;  // slots: last predictor, last corrector, the older entry
+  // frozen band size and the Krylov workspace of the g^{1/2}-split scheme
+  int fixed_count_ = 0;
+  void* kry_mem_ = nullptr;
+  long long kry_cap_ = 0;
+  int kld_ = 0, kry_dim_max_ = 0;
+  T *kV_ = nullptr, *kw_ = nullptr, *kR0_ = nullptr, *kb_ = nullptr, *kVt_ = nullptr, *ksg_ = nullptr, *kisg_ = nullptr;
+  double *kal_ = nullptr, *kbe_ = nullptr, *kacc_ = nullptr, *ky_ = nullptr, *knrm_ = nullptr;
 };
 
 }  // namespace etd

@@ -33,7 +33,7 @@ class ModelParams:
     n: tuple = (64, 64, 64)          # (Nx, Ny, Nz); Nz = 1 for dim = 2
     half_len: tuple = (math.pi, math.pi, math.pi)   # (X, Y, Z), box [-X, X)
     scheme: int = 2                  # 1 = ETD1, 2 = ETDRK2
-    model: int = 1                   # 0 = fixed membrane (Sec. 2), 1 = coupled (Sec. 3)
+    model: int = 1                   # 0 = fixed membrane (Sec. 3 split), 1 = coupled, 2 = fixed, Sec. 2.2 scheme
     precision: int = 0               # 0 = FP64, 1 = FP32 storage/FFT with FP64 tables/reductions
     tau: float = 1e-4
     eps_phi: float = 0.1
@@ -59,6 +59,7 @@ class ModelParams:
     cg_maxit: int = 20000
     linear_only: int = 0             # test mode: nonlinear terms R1 = R2 = 0
     cg_rtol_pred: float = 0.0        # ETDRK2 predictor-stage band solves (0: cg_rtol)
+    krylov_tol: float = 0.0          # model 2: Krylov error estimate tolerance (0: 1e-12 FP64, 1e-6 FP32)
 
     @property
     def shape(self):

@@ -71,7 +71,8 @@ def _plan_status(lib, p):
 @pytest.mark.parametrize("change", [
     dict(dim=4), dict(n=(48, 64, 64)), dict(n=(512, 64, 64)), dict(n=(64, 64, 4)), dict(n=(64, 192, 64)),
     dict(half_len=(math.pi, 2.0, math.pi)), dict(tau=0.0), dict(eps_u=-1.0), dict(scheme=3),
-    dict(precision=7), dict(cg_maxit=0), dict(band_mask_hi=1.5),
+    dict(precision=7), dict(cg_maxit=0), dict(band_mask_hi=1.5), dict(model=3),
+    dict(model=2, B2=0.0), dict(krylov_tol=-1.0), dict(krylov_tol=1.0),
 ])
 def test_invalid_parameters_rejected_without_gpu(lib, change):
     p = wl.workload("c3", n=64)[0].replace(**change)
@@ -84,3 +85,12 @@ def test_null_handling(lib):
     assert lib.etd_free(None) == 0
     assert lib.etd_step(None, None, None, 1, None) == 1
     assert lib.etd_plan(None, None, None) == 1
+
+
+def test_batch_rejects_the_sqrtg_model_without_gpu(lib):
+    good = wl.workload("c2", n=32)[0]
+    arr = (abi.etd_params * 2)(abi.params_struct(good), abi.params_struct(good.replace(model=2)))
+    h = ct.c_void_p(123)
+    code = lib.etd_plan_batch(arr, 2, None, 0, ct.byref(h))
+    assert code == 1 and h.value is None
+    assert "run 1" in lib.etd_last_error().decode()
