@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=19, help="steps of the FP64 comparison leg (0: skip)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
+    ap.add_argument("--no-sec2", action="store_true", help="skip the Sec. 2.2 Krylov-scheme leg")
     return ap.parse_args()
 
 
@@ -369,6 +370,48 @@ def batch_leg(stream, peak):
     }
 
 
+def sec2_leg(stream, peak):
+    """The g^{1/2}-split scheme of Sec. 2.2 (Lanczos phi_j(tau L) on the band) in the paper's 2D
+    rate-study setting: 256^2 on [-1,1]^2, circle, eps_phi = eps_u = 10 h, ETDRK2 (M = 200),
+    tau = 1e-4, FP64, band solve to 1e-11.  5 warm-up steps, then 100 steps timed with CUDA events;
+    a second pass of the same 100 steps with per-launch counters gives the time per kernel class
+    and the Krylov class's algorithmic bytes (15 elements + 24 B of couplings/indices per band
+    node per Lanczos step, plus the norms and combinations)."""
+    import torch
+    from paper_2606_04347_gb300 import Plan
+    from paper_2606_04347_gb300 import workloads as wl
+    p, phi, u0 = wl.paper2d("circle", 10.0, 2, 0)
+    p = p.replace(model=2, cg_rtol=1e-11)
+    plan = Plan(p, stream=stream)
+    u = torch.tensor(u0, device="cuda")
+    d = plan.step(torch.tensor(phi, device="cuda"), u, 5, diag=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nst = 100
+    e0.record(stream)
+    d = plan.step(None, u, nst, diag=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    plan.timing(True)
+    plan.step(None, u, nst)
+    kt = plan.timing_read()
+    plan.timing(False)
+    plan.close()
+    kms, kn, kb = kt["krylov"]
+    ach = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    return {
+        "workload": "Sec. 2.2 scheme, 2D 256^2 [-1,1]^2 circle, eps_phi = eps_u = 10h, ETDRK2, tau=1e-4, FP64",
+        "value": 256 * 256 * nst / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / nst,
+        "band_size": d["band_size"], "krylov_dim_last": d["krylov_dim_last"], "cg_iters_last": d["cg_iters_last"],
+        "kernel_ms_per_step": {k: round(v[0] / nst, 4) for k, v in kt.items() if v[1]},
+        "launches_per_step": {k: v[1] / nst for k, v in kt.items() if v[1]},
+        "krylov_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                            "algo_bytes_per_step": kb / nst,
+                            "note": "latency-bound: a band of ~5.7k nodes, host convergence check every 8 steps"},
+    }
+
+
 def run_ours(a):
     import torch
     rank, world, local = dist_env()
@@ -513,6 +556,9 @@ def run_ours(a):
     batch = None
     if not a.no_batch and rank == 0 and prec == 1:
         batch = batch_leg(stream, peak)
+    sec2 = None
+    if not a.no_sec2 and rank == 0:
+        sec2 = sec2_leg(stream, peak)
 
     # end to end through the public API with host buffers
     esize = 4 if prec else 8
@@ -559,6 +605,7 @@ def run_ours(a):
                               "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
             "fp64_gpu": fp64,
             "batch_c4": batch,
+            "sec2_2d": sec2,
             "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
             "kernel_ms_steps": a.steps, "timed_with_events_ms_per_step": ms_t / a.steps,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * npts * esize,
