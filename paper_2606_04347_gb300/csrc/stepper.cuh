@@ -309,6 +309,15 @@ template <typename T> class Stepper : public PlanBase {
     // that tests can make a wait run out and check the ETD_ETIMEOUT path
     if (const char* e = std::getenv("ETD_WAIT_BUDGET")) wait_budget_ = std::atoll(e);
     if (const char* e = std::getenv("ETD_WAIT_TRIES")) wait_tries_ = std::atoll(e);
+    // shape of the band solve's multigrid cycle (tuning; every choice is a symmetric V-cycle,
+    // so the preconditioned CG converges to the same tolerance): ETD_MG_LEVELS caps the levels,
+    // ETD_MG_GRID_CELLS is the full-grid size from which a level runs grid-wide (else on one
+    // block), ETD_MG_NU the smoothing sweeps per side (1 or 2), ETD_MG_CSWEEPS the Jacobi sweeps
+    // on the coarsest level (even)
+    if (const char* e = std::getenv("ETD_MG_LEVELS")) mg_maxlev_ = std::max(1, std::min(kMGMax, std::atoi(e)));
+    if (const char* e = std::getenv("ETD_MG_GRID_CELLS")) mg_grid_cells_ = std::max(1LL, std::atoll(e));
+    if (const char* e = std::getenv("ETD_MG_NU")) mg_nu_ = std::atoi(e) == 1 ? 1 : 2;
+    if (const char* e = std::getenv("ETD_MG_CSWEEPS")) mg_csweeps_ = std::max(2, std::atoi(e) / 2 * 2);
 
     // side stream and fork/join events of the band set-up overlap
     ETD_CUDA(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
@@ -851,7 +860,7 @@ template <typename T> class Stepper : public PlanBase {
     ETD_CUDA(cudaMemset(L0.t, 0, sizeof(T) * g_.n));
     mg_nlev_ = 1;
     const bool is3d = g_.nz > 1;
-    while (mg_nlev_ < kMGMax) {
+    while (mg_nlev_ < mg_maxlev_) {
       const HostLevel& F = lv_[mg_nlev_ - 1];
       // coarsen while every extent is even and at least 8
       auto ok = [](int v) { return v >= 8 && v % 2 == 0; };
@@ -878,7 +887,7 @@ template <typename T> class Stepper : public PlanBase {
       ++mg_nlev_;
     }
     mg_gl_ = 1;
-    while (mg_gl_ < mg_nlev_ && lv_[mg_gl_].cap >= (1 << 15)) ++mg_gl_;
+    while (mg_gl_ < mg_nlev_ && lv_[mg_gl_].cap >= mg_grid_cells_) ++mg_gl_;
   }
 
   // Coarse levels for the current band (level 0 = idx_, count_, mask_, bmap_, cg_).  Levels
@@ -955,8 +964,8 @@ template <typename T> class Stepper : public PlanBase {
     MGP<T> m{};
     m.nlev = mg_nlev_;
     m.gl = mg_gl_;
-    m.csweeps = 2;
-    m.nu = 2;
+    m.csweeps = mg_csweeps_;
+    m.nu = mg_nu_;
     // degree-2 Chebyshev weights for D^-1 A on [lmax / 4, lmax], lmax = 2 (Gershgorin bound
     // for the Jacobi-scaled graph Laplacian): w_i = 1 / (c + r cos((2 i + 1) pi / 4))
     {
@@ -1523,6 +1532,8 @@ template <typename T> class Stepper : public PlanBase {
   };
   HostLevel lv_[kMGMax];
   int mg_nlev_ = 1, mg_gl_ = 1;
+  int mg_maxlev_ = kMGMax, mg_nu_ = 2, mg_csweeps_ = 2;
+  long long mg_grid_cells_ = 1LL << 15;
   int *idx_ = nullptr, *idx_old_ = nullptr, *bcount_ = nullptr, *count_ = nullptr, *count_old_ = nullptr;
   int nblk_ = 0;
   T* tab_ = nullptr;

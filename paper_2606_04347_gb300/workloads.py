@@ -146,13 +146,17 @@ def _fixed_params(dim, n, eps_cfg, scheme, M, tau, precision):
 
 def _coupled_params(n, eps_cfg, tau, scheme, precision):
     # Coefficients of the paper's 3D run (Sec. 4.3) except the membrane friction mu, raised
-    # from 2 to 200: on this machine and interface width the explicit advection of g u by
+    # from 2 to 500: on this machine and interface width the explicit advection of g u by
     # v = -d_t phi grad phi/|grad phi|^2 is unstable at tau = 1e-4 with mu = 2 (|v| ~ 1e2
-    # to 1e5 at the band edge), and stays bounded with mu = 200 (|v| ~ 8).
+    # to 1e5 at the band edge).  With mu = 200 the membrane shrinks fast enough that U
+    # leaves [0, 1] (max|2U - 1| > 2 by step 100) and the run turns non-finite near step 475
+    # at 128^3 and 256^3 (FP64 and FP32 alike; tau = 5e-5 keeps it finite, so it is the time
+    # step's limit for the explicit terms); mu = 300 still leaves the bound at step 200;
+    # mu = 500 keeps max|2U - 1| <= 0.97 through 600 steps.
     eps_phi, eps_u = eps_from_cfg(eps_cfg)
     return ModelParams(dim=3, n=n, half_len=(math.pi,) * 3, scheme=scheme, model=1,
                        precision=precision, tau=tau, eps_phi=eps_phi, eps_u=eps_u,
-                       mu=200.0, lambda_surf=10.0, kappa=1.0, lambda_line=30.0,
+                       mu=500.0, lambda_surf=10.0, kappa=1.0, lambda_line=30.0,
                        M_area=100.0, A1=20.0, A2=50.0, M=3000.0, B1=1.0, B2=1000.0,
                        gamma=15000.0, alpha=700.0, ubar=0.3, u0=0.0)
 

@@ -6,9 +6,8 @@
   (tests/golden/c3_64_long.txt, written by tests/golden/make_c3_64_long.py from the oracle
   alone): max|2U - 1| over the recovery set and the volume <phi, 1>_h after every 25th step
   (the file's mass column, <G (U - ubar), 1>_h, is not what etd_energy reports: its mass is
-  the energy's <g (f(U) - ubar), 1>_h).  At these parameters the coupled flow loses the
-  maximum bound (max|2U - 1| passes 2 near step 100) and partly recovers it, and the mass
-  starts to grow fast near step 450; the GPU form has to follow the oracle through all of it.
+  the energy's <g (f(U) - ubar), 1>_h).  The run is the workload's full length; the GPU
+  form has to follow the oracle through all of it.
 """
 import os
 
