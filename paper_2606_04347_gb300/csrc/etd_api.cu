@@ -198,7 +198,7 @@ std::vector<etd::TileOpt> tile_candidates(const etd_params& p) {
   std::vector<etd::TileOpt> out;
   const int nz = p.dim == 2 ? 1 : p.n[2];
   const size_t csize = p.precision == ETD_FP64 ? 16 : 8;
-  const int zbs[3] = {1, 2, 4};
+  const int zbs[4] = {1, 2, 4, 8};
   for (int zb : zbs) {
     if (nz == 1 && zb != 1) continue;
     if (nz > 1 && (zb == 1 || nz % zb)) continue;
