@@ -238,6 +238,19 @@ etd_status etd_timing(etd_plan_t plan, int enable);
 etd_status etd_timing_read(etd_plan_t plan, int kind, double *total_ms, long *launches,
                            double *algo_bytes);
 
+/* ---- Host half of the Krylov evaluation (ETD_MODEL_FIXED_SQRTG) ------------------- */
+
+/* For the symmetric tridiagonal Lanczos matrix T_m (diagonal alpha[0..m-1], off-diagonal
+ * beta[0..m-2]; host arrays), writes y = phi_j(tau T_m) e_1 (m host doubles) and *tail =
+ * |e_m^T phi_{j+1}(tau T_m) e_1|, with phi_0(z) = e^{-z}, phi_1(z) = (1 - e^{-z})/z,
+ * phi_2(z) = (e^{-z} - 1 + z)/z^2, phi_3(z) = (1/2 - phi_2(z))/z (Sec. 2.2's convention).
+ * The plan of the Sec. 2.2 scheme takes tau phi_j(tau L) x ~ tau |x| V_m y and stops growing
+ * the Krylov space when |x| beta_m tau *tail is small against the result.  T_m by cyclic Jacobi
+ * rotations; 1 <= m <= 128, j in {0, 1, 2}, tau >= 0, T_m positive semi-definite (the phi_j
+ * series and closed forms are evaluated at tau lambda >= 0).  Host computation only: needs no GPU. */
+etd_status etd_krylov_coeffs(int m, const double *alpha, const double *beta, double tau, int j, double *y,
+                             double *tail);
+
 /* ---- Forward FFT that allocates nothing ------------------------------------------- */
 
 /* The paper has no counterpart to this entry point; it serves callers that may not

@@ -81,6 +81,8 @@ SIGNATURES.update({
     "etd_batch_free": (ct.c_int, [ct.c_void_p]),
 })
 
+SIGNATURES["etd_krylov_coeffs"] = (ct.c_int, [ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_double,
+                                               ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)])
 SIGNATURES["etd_fft_forward_noalloc"] = (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.c_int, ct.c_void_p,
                                                   ct.c_void_p, ct.c_void_p])
 
@@ -260,3 +262,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def krylov_coeffs(alpha, beta, tau, j):
+    """(y, tail) of etd_krylov_coeffs: y = phi_j(tau T) e_1 and |e_m^T phi_{j+1}(tau T) e_1| for the
+    tridiagonal T with diagonal alpha and off-diagonal beta (host computation, no GPU)."""
+    import numpy as np
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    m = a.size
+    b = np.ascontiguousarray(beta if m > 1 else [0.0], dtype=np.float64)
+    y = np.zeros(m)
+    tail = ct.c_double()
+    dp = ct.POINTER(ct.c_double)
+    _check(load_library().etd_krylov_coeffs(m, a.ctypes.data_as(dp), b.ctypes.data_as(dp), float(tau), int(j),
+                                            y.ctypes.data_as(dp), ct.byref(tail)))
+    return y, tail.value

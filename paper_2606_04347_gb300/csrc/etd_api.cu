@@ -8,6 +8,7 @@
 #include <tuple>
 #include <vector>
 #include "fft.cuh"
+#include "krylov.cuh"
 #include "plan.h"
 
 struct etd_plan_s {
@@ -180,6 +181,19 @@ etd_status etd_timing_read(etd_plan_t plan, int kind, double* total_ms, long* la
   if (!plan || !total_ms || !launches || !algo_bytes) return fail(ETD_EINVAL, "NULL argument");
   if (kind < 0 || kind >= ETD_K_NKINDS) return fail(ETD_EINVAL, "unknown kernel kind");
   return guard([&] { plan->impl->timing_read(kind, total_ms, launches, algo_bytes); });
+}
+
+etd_status etd_krylov_coeffs(int m, const double* alpha, const double* beta, double tau, int j, double* y,
+                             double* tail) {
+  if (m < 1 || m > etd::kKrylovMax) return fail(ETD_EINVAL, "m must be in [1, 128]");
+  if (j < 0 || j > 2) return fail(ETD_EINVAL, "j must be 0, 1 or 2");
+  if (!alpha || (m > 1 && !beta) || !y || !tail) return fail(ETD_EINVAL, "NULL argument");
+  if (!(tau >= 0)) return fail(ETD_EINVAL, "tau must be >= 0");
+  return guard([&] {
+    std::vector<double> v;
+    *tail = etd::krylov_coeffs(m, alpha, beta, tau, j, v);
+    for (int k = 0; k < m; ++k) y[k] = v[k];
+  });
 }
 
 }  // extern "C"
