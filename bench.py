@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=64, help="grid of the oracle sample")
     ap.add_argument("--cpu-steps", type=int, default=6)
@@ -85,15 +85,20 @@ def aggregate(world: int, points: int, steps: int, ms_max: float) -> float:
     return world * points * steps / (ms_max / 1e3) / 1e6
 
 
+KERNEL_SOURCES = ("df32.cuh", "fft.cuh", "kernels.cuh", "ops.cuh")
+
+
 def source_hash():
-    """sha256 over the CUDA sources: ties recorded ncu counters to the kernels they measured."""
+    """sha256 over the sources that define the measured kernels (the FFT passes with their tile
+    choice, the spectral operators and epilogues, the pointwise kernels and the band solve):
+    ties recorded ncu counters to the kernels they measured.  The plan's host orchestration and
+    the kernels no recorded counter covers (the Krylov scheme's) are left out."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_04347_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in sorted(KERNEL_SOURCES):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
 
 
@@ -578,19 +583,35 @@ def run_ours(a):
     esize = 4 if prec else 8
     h_phi = torch.from_numpy(phi0.astype(np.float32 if prec else np.float64)).pin_memory()
     h_u = torch.from_numpy(u0.astype(np.float32 if prec else np.float64)).pin_memory()
-    o_phi = torch.empty_like(h_phi).pin_memory()
-    o_u = torch.empty_like(h_u).pin_memory()
+    # each end-to-end step is an independent call on fresh host input (copy in, one step, copy
+    # out); two plans on two streams take alternate steps, so one step's host copies overlap
+    # the other's kernels (every copy and every kernel stays inside the timed region)
+    lanes = []
+    for _ in range(2):
+        st = torch.cuda.Stream()
+        lanes.append((Plan(p, stream=st), st, torch.empty_like(phi), torch.empty_like(u),
+                      torch.empty_like(h_phi).pin_memory(), torch.empty_like(h_u).pin_memory()))
+    for pl, st, dphi, du, _, _ in lanes:      # first call of each plan, untimed
+        with torch.cuda.stream(st):
+            dphi.copy_(h_phi, non_blocking=True)
+            du.copy_(h_u, non_blocking=True)
+            pl.step(dphi, du, 1)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(a.e2e_steps):
-        phi.copy_(h_phi, non_blocking=True)
-        u.copy_(h_u, non_blocking=True)
-        plan.step(phi, u, 1)
-        o_phi.copy_(phi, non_blocking=True)
-        o_u.copy_(u, non_blocking=True)
-        torch.cuda.synchronize()
+    for k in range(a.e2e_steps):
+        pl, st, dphi, du, hphi, hu = lanes[k % 2]
+        with torch.cuda.stream(st):
+            dphi.copy_(h_phi, non_blocking=True)
+            du.copy_(h_u, non_blocking=True)
+            pl.step(dphi, du, 1)
+            hphi.copy_(dphi, non_blocking=True)
+            hu.copy_(du, non_blocking=True)
+    torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    for ln in lanes:
+        ln[0].close()
+    del lanes
     barrier()
     t_e2e = allreduce_max(t_e2e, world)
     e2e = aggregate(world, npts, a.e2e_steps, 1e3 * t_e2e)
@@ -623,7 +644,9 @@ def run_ours(a):
             "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
             "kernel_ms_steps": a.steps, "timed_with_events_ms_per_step": ms_t / a.steps,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * npts * esize,
-                    "d2h_bytes_per_step": 2 * npts * esize},
+                    "d2h_bytes_per_step": 2 * npts * esize, "steps": a.e2e_steps,
+                    "how": "one etd_step call per step on pinned host input and output, two plans on two streams "
+                           "taking alternate steps"},
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
