@@ -130,7 +130,9 @@ etd_status etd_step(etd_plan_t plan, void *phi, void *u, int nsteps, etd_diag *l
 
 /* Diagnostics of (phi, u): energy of Eq. (2.16) (nonlocal term by a band solve of
  * (-Delta_{S,h}) w = g f(U) - mean), the energy's mass <g (f(U) - ubar), 1>_h (both models),
- * bound statistics, volume.  Synchronous. */
+ * bound statistics, volume.  Plans of ETD_MODEL_FIXED_SQRTG report the same quantity (its
+ * gradient term over every face of the grid), not the band system's own energy, whose gradient
+ * term counts band faces only.  Synchronous. */
 etd_status etd_energy(etd_plan_t plan, const void *phi, const void *u, etd_diag *out);
 
 /* Release the plan and its workspace.  etd_free(NULL) returns ETD_OK. */
