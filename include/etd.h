@@ -85,7 +85,9 @@ typedef struct {
                               at a time, at most 128) until the estimated error of
                               tau phi_j(tau L_phi) x, |x| beta_m tau |e_m^T phi_{j+1}(tau T_m) e_1|,
                               is below krylov_tol times the result's norm; 0 = 1e-12 (FP64),
-                              1e-6 (FP32-mixed).  Ignored by the other models.              */
+                              1e-6 (FP32-mixed); a space that reaches 128 steps without it
+                              makes etd_step return ETD_ENOTCONV.  Ignored by the other
+                              models.                                                       */
 } etd_params;
 
 /* Diagnostics of the current state (Eq. (2.16) energy and the bound of Sec. 2.2). */
